@@ -1,0 +1,168 @@
+/*
+ * stencil.h - C ABI of the GB300-native FP64 stencil library.
+ *
+ * The library advances regular FP64 grids by T steps of a Jacobi or
+ * Gauss-Seidel stencil, the computation classified in Section 1 of
+ * "Temporal Vectorization for Stencils" (dimension, order, star or box
+ * shape, Jacobi or Gauss-Seidel dependence, constant or periodic boundary)
+ * and written as the naive (d+1)-loop code of Algorithm 1.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid layout: interior points only, C order, ext[0] the slowest dimension
+ *   and ext[dim-1] the contiguous one; unused trailing ext[] entries are
+ *   ignored. Data pointers are DEVICE pointers unless a name says "host".
+ * Offsets: a stencil of radius r holds the offsets o in [-r, r]^dim; a star
+ *   keeps those with at most one non-zero component, a box keeps all.
+ *   "Canonical order" sorts them lexicographically, slowest dimension first.
+ *   Coefficients are passed in canonical order.
+ * Update: u'[p] = sum_o w_o * u[B(p + o)], the terms summed in DESCENDING
+ *   canonical order. B is the boundary rule: a constant boundary reads the
+ *   value c at every index outside the grid (corners included); a periodic
+ *   boundary wraps every index modulo its extent.
+ * Jacobi (Algorithm 1): every point of step t+1 reads step-t values only.
+ * Gauss-Seidel (Section 3.4): one array updated in place, points visited in
+ *   increasing lexicographic order, so already-visited neighbours contribute
+ *   their newest value (Section 3.2: the space loop runs in increasing order).
+ * Arithmetic: STENCIL_ARITH_FMA rounds the first product, then adds each
+ *   further term with one fused multiply-add. STENCIL_ARITH_UNFUSED rounds
+ *   every product and every sum. Both are bit-for-bit reproducible.
+ * Streams: every run is asynchronous and stream-ordered on the given
+ *   cudaStream_t (NULL = legacy default stream). Inputs must stay valid until
+ *   the stream reaches the run.
+ * Errors: synchronous argument and launch errors are returned as negative
+ *   codes. Errors that happen on the device while a kernel runs (a bounded
+ *   wait that gave up) are recorded in the handle's status word and returned
+ *   by stencil_status(). No entry point aborts the process or traps the GPU.
+ * Threads: a handle is not thread-safe; distinct handles may be used from
+ *   different threads and streams at once.
+ */
+#ifndef GB300_STENCIL_H
+#define GB300_STENCIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define STENCIL_OK 0
+#define STENCIL_EINVAL (-1)       /* invalid argument */
+#define STENCIL_EUNSUPPORTED (-2) /* valid but not supported (dim > 3, r > 4, ...) */
+#define STENCIL_ENOMEM (-3)       /* device allocation failed */
+#define STENCIL_ECUDA (-4)        /* a CUDA call or kernel launch failed */
+#define STENCIL_ETIMEOUT (-5)     /* a device-side bounded wait gave up */
+#define STENCIL_EBOUNDS (-6)      /* a device-side index check failed */
+
+/* Stencil shape (Section 1 taxonomy). */
+#define STENCIL_STAR 0
+#define STENCIL_BOX 1
+/* Dependence type (Section 1 taxonomy; Section 3.4). */
+#define STENCIL_JACOBI 0
+#define STENCIL_GAUSS_SEIDEL 1
+/* Boundary condition (Section 1 taxonomy). */
+#define STENCIL_BC_CONSTANT 0
+#define STENCIL_BC_PERIODIC 1
+/* Rounding of the weighted sum. */
+#define STENCIL_ARITH_FMA 0
+#define STENCIL_ARITH_UNFUSED 1
+
+/* Kernel families a run may use (stencil_set_plan). */
+#define STENCIL_KERNEL_AUTO 0      /* autotuned choice (default) */
+#define STENCIL_KERNEL_PLAIN 1     /* one launch per Jacobi step / Gauss-Seidel sweep */
+#define STENCIL_KERNEL_BLOCKED 2   /* Jacobi: tile + halo staged in shared memory, T_b steps per pass */
+#define STENCIL_KERNEL_WAVEFRONT 3 /* Gauss-Seidel: time-skewed wavefront, warp lanes hold sweeps */
+
+typedef struct stencil_handle_s* stencil_handle; /* opaque, owned by the library */
+
+typedef struct {
+    double* data;     /* device pointer, the grid; holds the result after the run */
+    int64_t ext[3];   /* extents, ext[0] slowest; entries beyond dim are ignored */
+    double* scratch;  /* device pointer to workspace of stencil_workspace_bytes() bytes, or NULL */
+} stencil_grid;
+
+/*
+ * Create a stencil.
+ *   dim            1, 2 or 3.
+ *   shape          STENCIL_STAR or STENCIL_BOX.
+ *   radius         1..4 (the paper's kernels use 1).
+ *   coeffs/ncoeffs host array of the K weights in canonical order; K must be
+ *                  2*dim*radius+1 (star) or (2*radius+1)^dim (box). Copied.
+ *   method         STENCIL_JACOBI or STENCIL_GAUSS_SEIDEL.
+ *   boundary       STENCIL_BC_CONSTANT (value boundary_value) or STENCIL_BC_PERIODIC.
+ *   arith          STENCIL_ARITH_FMA or STENCIL_ARITH_UNFUSED.
+ *   out            receives the handle.
+ * Allocates a small device block (weights, offsets, status word) on the
+ * current device. Returns STENCIL_OK, EINVAL, EUNSUPPORTED, ENOMEM or ECUDA.
+ */
+int stencil_create(int dim, int shape, int radius, const double* coeffs, int ncoeffs, int method,
+                   int boundary, double boundary_value, int arith, stencil_handle* out);
+
+/*
+ * Fix the kernel family and its parameters instead of the autotuned choice.
+ *   kernel   STENCIL_KERNEL_* (AUTO restores the default).
+ *   tb       temporal block depth T_b (BLOCKED) or sweeps per warp (WAVEFRONT,
+ *            1..32); 0 = default.
+ *   tile     tile extents (slowest first) for BLOCKED, 0 = default.
+ * A family that cannot run a given (method, boundary, grid) makes stencil_run
+ * return EUNSUPPORTED.
+ */
+int stencil_set_plan(stencil_handle h, int kernel, int tb, const int64_t tile[3]);
+
+/*
+ * Advance g by T >= 0 steps (Jacobi) or sweeps (Gauss-Seidel) on stream
+ * (a cudaStream_t). T = 0 returns at once. Jacobi needs workspace of one grid:
+ * g->scratch if not NULL (stencil_workspace_bytes bytes, not aliasing data),
+ * else the library allocates it stream-ordered and frees it after the run.
+ * Periodic boundaries need every used extent >= 2*radius+1.
+ * Returns STENCIL_OK or a negative code; device-side failures are reported
+ * later by stencil_status().
+ */
+int stencil_run(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_stream);
+
+/*
+ * Run n independent problems (h[i], g[i], T[i]) with as few launches as
+ * possible: the Jacobi steps of every problem are walked by one persistent
+ * kernel per pass over a shared work list, replayed from a CUDA graph that
+ * is cached on the batch's shape. Every g[i] needs its scratch set. The
+ * results equal n separate stencil_run calls bit for bit.
+ */
+int stencil_run_batch(const stencil_handle* h, const stencil_grid* g, const int64_t* T, int n,
+                      void* cuda_stream);
+
+/* Bytes of workspace stencil_run needs for g (0 for Gauss-Seidel). */
+int stencil_workspace_bytes(stencil_handle h, const stencil_grid* g, size_t* bytes);
+
+/*
+ * Synchronise stream, then return and clear the handle's device status:
+ * STENCIL_OK, STENCIL_ETIMEOUT or STENCIL_EBOUNDS (or ECUDA if the
+ * synchronisation itself failed).
+ */
+int stencil_status(stencil_handle h, void* cuda_stream);
+
+/* Release the handle and its device block (after its runs have finished). */
+int stencil_destroy(stencil_handle h);
+
+/* Static English text for a return code. */
+const char* stencil_strerror(int code);
+
+/*
+ * End-to-end convenience over host memory: copy host_data (ext[0]*..*ext[dim-1]
+ * doubles, pinned or pageable) to dev_data, run T steps, copy the result back
+ * to host_data. dev_data and dev_scratch are caller-owned device buffers of one
+ * grid each (dev_scratch may be NULL as in stencil_run). Synchronises stream
+ * before returning, so host_data holds the result on return.
+ */
+int stencil_run_host(stencil_handle h, double* host_data, const int64_t ext[3], double* dev_data,
+                     double* dev_scratch, int64_t T, void* cuda_stream);
+
+/* Number of kernels this library has launched since load (all handles). */
+uint64_t stencil_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_STENCIL_H */

@@ -1,0 +1,183 @@
+// Device-side building blocks shared by the stencil kernels.
+//
+// A stencil point update (Section 1; Algorithm 1) is the weighted sum of the
+// neighbours at the canonical offsets, summed in DESCENDING canonical order:
+// the offset that is largest lexicographically (slowest dimension first)
+// comes first, so that in Gauss-Seidel the newest-value terms (negative
+// offsets) come last. Two rounding modes:
+//   ARITH_FMA      acc = w0*v0 (rounded), then acc = fma(wq, vq, acc)
+//   ARITH_UNFUSED  acc = w0*v0 (rounded), then acc = acc + (wq*vq), each rounded
+// The intrinsics __dmul_rn / __fma_rn / __dadd_rn pin every rounding; the
+// compiler never contracts them.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gbst {
+
+enum { STAR = 0, BOX = 1 };
+enum { JACOBI = 0, GAUSS_SEIDEL = 1 };
+enum { BC_CONSTANT = 0, BC_PERIODIC = 1 };
+enum { ARITH_FMA = 0, ARITH_UNFUSED = 1 };
+
+// Device status word values (mirrored by the C ABI's negative codes).
+enum { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BOUNDS = 2 };
+
+// Extents padded to three dimensions, slowest first (a 1D grid is 1 x 1 x N).
+struct Geo {
+    int64_t n0, n1, n2;
+};
+
+// Stencil description for kernels that take the offsets at run time.
+struct StencilDev {
+    int K, r, bc, arith;
+    double c;
+    const double* w;   // K weights, descending canonical order (device)
+    const int* off;    // 3K offset components, descending canonical order (device)
+    int* status;       // device status word
+};
+
+__host__ __device__ constexpr int stencil_k(int dim, int shape, int r)
+{
+    return shape == STAR ? 2 * dim * r + 1 : (dim == 1 ? 2 * r + 1 : (dim == 2 ? (2 * r + 1) * (2 * r + 1)
+                                                                              : (2 * r + 1) * (2 * r + 1) * (2 * r + 1)));
+}
+
+// Component d (0..2, slowest first, padded) of canonical offset q of a star.
+// Canonical (lexicographic) order of a star: the negative offsets of each axis
+// from the slowest axis to the second fastest, then the fastest axis from -r
+// to +r, then the positive offsets from the second fastest axis back to the
+// slowest.
+__host__ __device__ constexpr int star_off(int dim, int r, int q, int d)
+{
+    int first = 3 - dim;
+    int idx = q;
+    for (int a = first; a < 2; ++a) {
+        if (idx < r) return d == a ? idx - r : 0;
+        idx -= r;
+    }
+    if (idx < 2 * r + 1) return d == 2 ? idx - r : 0;
+    idx -= 2 * r + 1;
+    for (int a = 1; a >= first; --a) {
+        if (idx < r) return d == a ? idx + 1 : 0;
+        idx -= r;
+    }
+    return 0;
+}
+
+// Component d of canonical offset q of a box: q written in base 2r+1, the
+// slowest used axis the most significant digit.
+__host__ __device__ constexpr int box_off(int dim, int r, int q, int d)
+{
+    if (d < 3 - dim) return 0;
+    int b = 2 * r + 1;
+    int v = q;
+    for (int i = 0; i < 2 - d; ++i) v /= b;
+    return v % b - r;
+}
+
+template <int DIM, int SHAPE, int R>
+struct Stn {
+    static constexpr int K = stencil_k(DIM, SHAPE, R);
+    // offset component d of the q-th term in summation (descending) order
+    __host__ __device__ static constexpr int o(int q, int d)
+    {
+        return SHAPE == STAR ? star_off(DIM, R, K - 1 - q, d) : box_off(DIM, R, K - 1 - q, d);
+    }
+};
+
+template <int K>
+struct WArr {
+    double w[K];  // descending canonical order
+};
+
+template <int ARITH>
+__device__ __forceinline__ double acc_step(double acc, double w, double v)
+{
+    if (ARITH == ARITH_FMA) return __fma_rn(w, v, acc);
+    return __dadd_rn(acc, __dmul_rn(w, v));
+}
+
+__device__ __forceinline__ int64_t wrap_idx(int64_t i, int64_t n)
+{
+    // |offset| <= r < n for periodic grids, so one correction suffices
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// Value at (i, j, k) under the boundary rule; u is read with a plain
+// (coherent) load so that values written earlier in the same kernel by this
+// CTA are seen.
+__device__ __forceinline__ double fetch_bc(const double* u, int64_t i, int64_t j, int64_t k, const Geo& g,
+                                           int bc, double c)
+{
+    if (bc == BC_PERIODIC) {
+        i = wrap_idx(i, g.n0);
+        j = wrap_idx(j, g.n1);
+        k = wrap_idx(k, g.n2);
+    } else if (i < 0 || i >= g.n0 || j < 0 || j >= g.n1 || k < 0 || k >= g.n2) {
+        return c;
+    }
+    return u[(i * g.n1 + j) * g.n2 + k];
+}
+
+// Full update at (i, j, k) with compile-time offsets and the boundary rule
+// applied to every term.
+template <int DIM, int SHAPE, int R, int ARITH>
+__device__ __forceinline__ double update_bc(const double* u, int64_t i, int64_t j, int64_t k, const Geo& g,
+                                            int bc, double c, const double* w)
+{
+    using S = Stn<DIM, SHAPE, R>;
+    double v[S::K];
+#pragma unroll
+    for (int q = 0; q < S::K; ++q) v[q] = fetch_bc(u, i + S::o(q, 0), j + S::o(q, 1), k + S::o(q, 2), g, bc, c);
+    double acc = __dmul_rn(w[0], v[0]);
+#pragma unroll
+    for (int q = 1; q < S::K; ++q) acc = acc_step<ARITH>(acc, w[q], v[q]);
+    return acc;
+}
+
+// Full update at linear index p whose every neighbour is inside the grid.
+template <int DIM, int SHAPE, int R, int ARITH, bool RO>
+__device__ __forceinline__ double update_interior(const double* u, int64_t p, int64_t s0, int64_t s1,
+                                                  const double* w)
+{
+    using S = Stn<DIM, SHAPE, R>;
+    double v[S::K];
+#pragma unroll
+    for (int q = 0; q < S::K; ++q) {
+        const double* a = u + p + S::o(q, 0) * s0 + S::o(q, 1) * s1 + S::o(q, 2);
+        v[q] = RO ? __ldg(a) : *a;
+    }
+    double acc = __dmul_rn(w[0], v[0]);
+#pragma unroll
+    for (int q = 1; q < S::K; ++q) acc = acc_step<ARITH>(acc, w[q], v[q]);
+    return acc;
+}
+
+// Run-time-offset update (any K), the boundary rule applied to every term.
+template <int ARITH>
+__device__ __forceinline__ double update_rt(const double* u, int64_t i, int64_t j, int64_t k, const Geo& g,
+                                            const StencilDev& s)
+{
+    double acc = 0.0;
+    for (int q0 = 0; q0 < s.K; q0 += 8) {
+        double v[8];
+        double w[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            int q = q0 + t;
+            if (q < s.K) {
+                v[t] = fetch_bc(u, i + s.off[3 * q], j + s.off[3 * q + 1], k + s.off[3 * q + 2], g, s.bc, s.c);
+                w[t] = s.w[q];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            int q = q0 + t;
+            if (q < s.K) acc = (q == 0) ? __dmul_rn(w[t], v[t]) : acc_step<ARITH>(acc, w[t], v[t]);
+        }
+    }
+    return acc;
+}
+
+}  // namespace gbst

@@ -1,0 +1,59 @@
+// Host-side internals shared by the C ABI and the kernel launchers.
+#pragma once
+#include <atomic>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/stencil.h"
+#include "common.cuh"
+
+struct stencil_handle_s {
+    int dim, shape, r, K, method, bc, arith;
+    double c;
+    std::vector<double> w_desc;  // weights, descending canonical order
+    std::vector<int> off_desc;   // 3 components per offset (padded, slowest first), same order
+    double* d_w = nullptr;       // device copies of the two tables
+    int* d_off = nullptr;
+    int* d_status = nullptr;     // device status word
+    int plan_kernel = STENCIL_KERNEL_AUTO;
+    int plan_tb = 0;
+    int64_t plan_tile[3] = {0, 0, 0};
+    int device = 0;
+};
+
+namespace gbst {
+
+extern std::atomic<uint64_t> g_launches;
+
+struct RunCtx {
+    stencil_handle_s* h;
+    Geo g;
+    cudaStream_t st;
+    StencilDev sd;
+};
+
+inline int cuda_rc(cudaError_t e) { return e == cudaSuccess ? STENCIL_OK : STENCIL_ECUDA; }
+
+// True if the plain kernels have a compile-time specialisation for (dim, shape, r).
+bool plain_specialised(int dim, int shape, int r);
+
+// One Jacobi step in -> out (plain, one launch).
+int jacobi_plain_step(const RunCtx& ctx, const double* in, double* out);
+// T Gauss-Seidel sweeps in place (plain: one sweep at a time).
+int gs_plain_run(const RunCtx& ctx, double* u, int64_t T);
+
+// Temporally blocked Jacobi: T steps from a (=g.data) using b (=scratch); the
+// result ends in a. Returns EUNSUPPORTED if the configuration is not covered.
+int jacobi_blocked_run(const RunCtx& ctx, double* a, double* b, int64_t T, int tb, const int64_t tile[3]);
+bool jacobi_blocked_supported(const stencil_handle_s* h, const Geo& g);
+
+// Time-skewed wavefront Gauss-Seidel: T sweeps in place.
+int gs_wavefront_run(const RunCtx& ctx, double* u, int64_t T, int lanes);
+bool gs_wavefront_supported(const stencil_handle_s* h, const Geo& g);
+
+// Geometry from a stencil_grid (padded to three dimensions).
+Geo make_geo(int dim, const int64_t ext[3]);
+
+}  // namespace gbst

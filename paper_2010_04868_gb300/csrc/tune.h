@@ -1,0 +1,19 @@
+// Plan selection (kernel family and its parameters) and the batched runner.
+#pragma once
+#include "internal.h"
+
+namespace gbst {
+
+struct Plan {
+    int kernel;       // STENCIL_KERNEL_PLAIN / BLOCKED / WAVEFRONT
+    int tb;           // temporal block depth (blocked) or sweeps per warp (wavefront)
+    int64_t tile[3];  // tile extents for the blocked kernel, slowest first
+};
+
+// The plan a run uses: the handle's fixed plan if set, else the tuned one.
+Plan plan_for(const stencil_handle_s* h, const Geo& g, int64_t T);
+
+// Batched execution of n problems (see stencil_run_batch).
+int batch_run(const stencil_handle* h, const stencil_grid* g, const int64_t* T, int n, cudaStream_t st);
+
+}  // namespace gbst

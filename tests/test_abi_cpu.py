@@ -1,0 +1,46 @@
+"""CPU-side checks of the CUDA library: it builds, loads, and exports what the header declares."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(stencil_[a-z_]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2010_04868_gb300 import build, stencil
+    build.build()
+    lib = stencil.load()
+    declared = _declared()
+    assert declared, "no declarations found"
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert declared == set(stencil.EXPORTS)
+
+
+def test_strerror_covers_codes():
+    from paper_2010_04868_gb300 import stencil
+    for code in range(0, -7, -1):
+        assert stencil.strerror(code) != "unknown error code"
+    assert stencil.strerror(-99) == "unknown error code"
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2010_04868_gb300 import stencil
+    saved = stencil._lib
+    stencil._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            stencil.load(str(tmp_path / "nope.so"))
+    finally:
+        stencil._lib = saved
