@@ -161,6 +161,25 @@ int stencil_run_host(stencil_handle h, double* host_data, const int64_t ext[3], 
 /* Number of kernels this library has launched since load (all handles). */
 uint64_t stencil_launch_count(void);
 
+/*
+ * Jacobi run that allocates nothing (the paper has no counterpart; this is a
+ * library service). For callers that may not allocate device memory: code
+ * under a device-memory budget fixed in advance, real-time loops that must
+ * not enter the CUDA allocator, host code running where allocation is
+ * forbidden. Same result as stencil_run with the plain kernel; g->scratch is
+ * ignored and the second Jacobi buffer is a fixed 16 MiB array inside the
+ * library, held by every GPU that loads the library until the process exits.
+ *   h        a Jacobi handle created on the current device (else EINVAL).
+ *   g        grid of at most 2^21 points (2,097,152); larger grids return
+ *            STENCIL_EUNSUPPORTED without touching the GPU.
+ *   T        steps, >= 0.
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller. The first call on each device looks up the
+ * array's device address and should come before any stream capture begins.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ */
+int stencil_run_noalloc(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

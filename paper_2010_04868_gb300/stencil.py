@@ -29,7 +29,11 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgb300ste
 
 #: Every entry point that include/stencil.h declares.
 EXPORTS = ("stencil_create", "stencil_set_plan", "stencil_run", "stencil_run_batch", "stencil_workspace_bytes",
-           "stencil_status", "stencil_destroy", "stencil_strerror", "stencil_run_host", "stencil_launch_count")
+           "stencil_status", "stencil_destroy", "stencil_strerror", "stencil_run_host", "stencil_launch_count",
+           "stencil_run_noalloc")
+
+#: Largest grid (points) stencil_run_noalloc accepts: its fixed workspace holds 2^21 doubles.
+NOALLOC_MAX_POINTS = 1 << 21
 
 
 class stencil_grid(ctypes.Structure):
@@ -58,6 +62,7 @@ def load(path: str = LIB_PATH):
     lib.stencil_strerror.argtypes = [I]
     lib.stencil_strerror.restype = ctypes.c_char_p
     lib.stencil_run_host.argtypes = [P, P, ctypes.POINTER(I64), P, P, I64, P]
+    lib.stencil_run_noalloc.argtypes = [P, ctypes.POINTER(stencil_grid), I64, P]
     lib.stencil_launch_count.argtypes = []
     lib.stencil_launch_count.restype = ctypes.c_uint64
     for name in EXPORTS:
@@ -134,6 +139,23 @@ def stencil_run_host(h, host_ptr, ext, dev_data_ptr, dev_scratch_ptr, T, stream_
     e = (ctypes.c_int64 * 3)(*(list(ext) + [1] * (3 - len(ext))))
     return check(load().stencil_run_host(h, host_ptr, e, dev_data_ptr, dev_scratch_ptr, int(T), stream_ptr),
                  "stencil_run_host")
+
+
+def stencil_run_noalloc(h, grid: stencil_grid, T, stream_ptr=None):
+    """Jacobi run whose workspace is the library's fixed 16 MiB array: no device allocation.
+
+    For callers that may not allocate device memory. Grids above
+    NOALLOC_MAX_POINTS points are rejected; calls that overlap on the GPU race
+    on the shared array.
+    """
+    rc = load().stencil_run_noalloc(h, ctypes.byref(grid), int(T), stream_ptr)
+    if rc == STENCIL_EUNSUPPORTED:
+        npts = 1
+        for e in grid.ext:
+            npts *= max(1, int(e))
+        raise StencilError(rc, "stencil_run_noalloc: grid of %d points exceeds the %d-point no-allocation "
+                               "workspace (or the handle is not supported)" % (npts, NOALLOC_MAX_POINTS))
+    return check(rc, "stencil_run_noalloc")
 
 
 def stencil_launch_count() -> int:
