@@ -162,6 +162,17 @@ int stencil_run_host(stencil_handle h, double* host_data, const int64_t ext[3], 
 uint64_t stencil_launch_count(void);
 
 /*
+ * Failure-detection test hook (no counterpart in the paper). The next
+ * wavefront Gauss-Seidel run of h never publishes the completion of one unit
+ * of work: tile number `unit` in the 2D/3D kernel's schedule order, or sweep
+ * block `unit` in 1D (-1 disables). Every wait on it gives up after `spin`
+ * polls (0 = the default limit, about two seconds), the kernel finishes, and
+ * stencil_status() then returns STENCIL_ETIMEOUT. The grid's contents after
+ * such a run are unspecified. Nothing faults, traps or hangs.
+ */
+int stencil_debug_inject_stall(stencil_handle h, int64_t unit, int spin);
+
+/*
  * Jacobi run that allocates nothing (the paper has no counterpart; this is a
  * library service). For callers that may not allocate device memory: code
  * under a device-memory budget fixed in advance, real-time loops that must

@@ -213,6 +213,7 @@ int stencil_destroy(stencil_handle h)
     cudaFree(h->d_w);
     cudaFree(h->d_off);
     cudaFree(h->d_status);
+    cudaFree(h->wave_ws);
     delete h;
     return STENCIL_OK;
 }
@@ -251,5 +252,13 @@ int stencil_run_host(stencil_handle h, double* host_data, const int64_t ext[3], 
 }
 
 uint64_t stencil_launch_count(void) { return g_launches.load(); }
+
+int stencil_debug_inject_stall(stencil_handle h, int64_t unit, int spin)
+{
+    if (!h || unit < -1 || spin < 0) return STENCIL_EINVAL;
+    h->debug_stall_tile = unit;
+    h->debug_spin = spin;
+    return STENCIL_OK;
+}
 
 }  // extern "C"

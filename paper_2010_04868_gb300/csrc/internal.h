@@ -17,6 +17,16 @@ struct stencil_handle_s {
     double* d_w = nullptr;       // device copies of the two tables
     int* d_off = nullptr;
     int* d_status = nullptr;     // device status word
+    // workspace of the wavefront Gauss-Seidel kernel (tile flags, schedule table,
+    // ticket counter), owned by the handle and grown on demand
+    void* wave_ws = nullptr;
+    size_t wave_ws_bytes = 0;
+    int wave_epoch = 0;
+    // failure-detection test hook: the next wavefront run never publishes the
+    // completion of this tile (2D/3D) or sweep block (1D); its waiters give up
+    // after debug_spin polls instead of the default limit
+    int64_t debug_stall_tile = -1;
+    int debug_spin = 0;
     int plan_kernel = STENCIL_KERNEL_AUTO;
     int plan_tb = 0;
     int64_t plan_tile[3] = {0, 0, 0};

@@ -1,7 +1,543 @@
-// Time-skewed wavefront Gauss-Seidel (placeholder until the kernel lands).
+// Time-skewed wavefront Gauss-Seidel: the lanes of a warp hold different sweeps.
+//
+// Temporal vectorization (Section 3.2, Algorithm 3) puts points with different
+// time coordinates into one vector: lane k holds sweep t0+k at a spatial
+// position s*k behind lane k-1, so one vector operation advances vl sweeps at
+// once. It is legal when the stride s exceeds every forward spatial distance
+// a dependence covers in one time step (Section 3.2); for the lexicographic
+// Gauss-Seidel update of radius r that means s >= r + 1. The same construction
+// applies to Gauss-Seidel stencils by taking the newest-value neighbours from
+// the output vectors (Section 3.4).
+//
+// On GB300 the vector is a warp (vl = 32 sweeps):
+//
+// 1D. Lane k of the warp for sweep block b updates x = n - s*k at step n.
+//     After each step it passes its output one lane up with __shfl_up_sync;
+//     that value is exactly the newest previous-sweep value lane k+1 needs
+//     next (the rotate + blend of Algorithm 3). Lane 0 loads its
+//     previous-sweep values from the grid (the "bottom vector") and the last
+//     lane stores the block's final sweep (the "top vector"); the sweeps in
+//     between never touch memory. Sweep blocks run concurrently, block b+1
+//     trailing block b through a progress word.
+//
+// 2D/3D. As in the paper, temporal vectorization runs along the outermost
+//     space loop (Section 3.2, high-dimensional stencils) and the skewed
+//     values of the inner loops go through memory. In block-relative skewed
+//     coordinates
+//         i2 = i + s*k,  j2 = j + a1*i + b1*k,  k2 = k' + a2*i + c2*j + b2*k
+//     (k the lane, i j k' the point) every neighbour a point reads as newest
+//     (same sweep) and every neighbour it reads as old (previous sweep, lane
+//     k-1) has skewed coordinates no larger than the point's own, and
+//     everything that will overwrite a value a point reads has larger ones.
+//     The skewed space is cut into tiles of H x HJ x W (2D: H x W); within a
+//     tile all lanes walk the skewed rows together (one step per row, the
+//     lanes independent within a step), each lane updating W points in order
+//     along the fast axis. Tiles form a DAG (a tile depends on its three
+//     lower neighbours and on a shifted tile of the previous sweep block: the
+//     paper's parallelogram tiling for Gauss-Seidel, Section 3.4); a
+//     persistent kernel hands out tiles in diagonal order through a ticket
+//     counter, and each tile waits (bounded) for its predecessors' flags.
+//
+// Every point is computed with the same descending-order sum and rounding as
+// the plain kernels, so results are bit-identical to T plain sweeps. Periodic
+// boundaries chain the end of each sweep to the start of the next and are left
+// to the plain kernel.
+#include <algorithm>
+#include <vector>
+
 #include "internal.h"
 
 namespace gbst {
-bool gs_wavefront_supported(const stencil_handle_s*, const Geo&) { return false; }
-int gs_wavefront_run(const RunCtx&, double*, int64_t, int) { return STENCIL_EUNSUPPORTED; }
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int SPIN_LIMIT = 1 << 22;  // x ~0.5 us sleep: a wait gives up after about two seconds
+
+// Bounded-wait settings of one launch: poll limit, and a tile/block whose
+// completion is never published (-1: none; used only by failure-detection tests).
+struct WaitCfg {
+    int spin;
+    int64_t stall;
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// --------------------------------------------------------------------- 1D ---
+
+constexpr int PROG_SHIFT = 40;
+constexpr unsigned long long PROG_MASK = (1ull << PROG_SHIFT) - 1;
+
+// Wait until the previous block has finalised positions [0, need); returns how
+// many it has (a large value after a time-out, which is recorded in status).
+__device__ __noinline__ int64_t wait_progress(const unsigned long long* p, int64_t need, unsigned tag, int* status,
+                                              int spin)
+{
+    for (int it = 0; it < spin; ++it) {
+        unsigned long long v = ld_acquire64(p);
+        if ((unsigned)(v >> PROG_SHIFT) == tag && (int64_t)(v & PROG_MASK) >= need) return (int64_t)(v & PROG_MASK);
+        __nanosleep(500);
+    }
+    atomicExch(status, DEV_TIMEOUT);
+    return INT64_MAX;
+}
+
+template <int R, int ARITH>
+__global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_t n, double c, WArr<2 * R + 1> w,
+                                                  int64_t T, unsigned long long* progress, int* ticket, int* status,
+                                                  unsigned tag, WaitCfg wc)
+{
+    constexpr int S = R + 1;
+    const int lane = threadIdx.x;
+    int b = 0;
+    if (lane == 0) b = atomicAdd(ticket, 1);
+    b = __shfl_sync(FULL, b, 0);
+    const int64_t nB = (T + 31) / 32;
+    if (b >= nB) return;
+    const int L = (int)((T - 32 * (int64_t)b) < 32 ? (T - 32 * (int64_t)b) : 32);
+    const bool top = lane == L - 1;
+    const unsigned long long* prev = b > 0 ? progress + b - 1 : nullptr;
+    unsigned long long* mine = progress + b;
+    const bool publish = b != wc.stall;
+    const unsigned long long mytag = (unsigned long long)tag << PROG_SHIFT;
+    int64_t known = b > 0 ? 0 : INT64_MAX;
+
+    // old[o]: previous-sweep value at x - 1 + o (before the step's receive);
+    // nw[a]: this sweep's value at x - 1 - a
+    double old[R + 1], nw[R];
+#pragma unroll
+    for (int o = 0; o <= R; ++o) {
+        const int64_t p = -1 + o;
+        old[o] = c;
+        if (lane == 0 && p >= 0 && p < n) {
+            if (p >= known) known = wait_progress(prev, p + 1, tag, status, wc.spin);
+            old[o] = __ldcg(u + p);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a) nw[a] = c;
+    double out = c;
+    const int64_t steps = n + (int64_t)S * (L - 1);
+    for (int64_t step = 0; step < steps; ++step) {
+        const int64_t x = step - (int64_t)S * lane;
+        double recv = __shfl_up_sync(FULL, out, 1);
+        if (lane == 0) {
+            const int64_t p = x + R;
+            recv = c;
+            if (p < n) {
+                // wait for a chunk ahead so the next waits are rare; never past the grid end
+                if (p >= known) known = wait_progress(prev, (p + 257 < n ? p + 257 : n), tag, status, wc.spin);
+                recv = __ldcg(u + p);
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < R; ++o) old[o] = old[o + 1];
+        old[R] = recv;
+        // descending canonical order: +R .. +1, 0 (previous sweep), -1 .. -R (this sweep)
+        double acc = __dmul_rn(w.w[0], old[R]);
+#pragma unroll
+        for (int q = 1; q <= R; ++q) acc = acc_step<ARITH>(acc, w.w[q], old[R - q]);
+#pragma unroll
+        for (int a = 1; a <= R; ++a) acc = acc_step<ARITH>(acc, w.w[R + a], nw[a - 1]);
+        const bool inside = x >= 0 && x < n;
+        out = inside ? acc : c;
+#pragma unroll
+        for (int a = R - 1; a > 0; --a) nw[a] = nw[a - 1];
+        nw[0] = out;
+        if (top) {
+            if (inside) u[x] = acc;
+            if (publish && (step & 63) == 63 && x >= 0) {
+                __threadfence();
+                st_release64(mine, mytag | (unsigned long long)(x + 1 < n ? x + 1 : n));
+            }
+        }
+    }
+    if (top && publish) {
+        __threadfence();
+        st_release64(mine, mytag | (unsigned long long)n);
+    }
+}
+
+// ------------------------------------------------------------------ 2D/3D ---
+
+struct WaveGeo {
+    int s, a1, b1, a2, c2, b2;   // skew (see the file comment); 2D uses s, a1, b1
+    int H, HJ;                   // tile extents on i2 and (3D) j2; the fast axis extent is the template W
+    int64_t nI, nJ, nK, nB;      // tiles per skewed axis, sweep blocks
+    int dI, dJ, dK, db;          // shift of the previous-block dependency, block weight of the diagonal index
+    int64_t T, ntiles, nD;
+};
+
+__device__ __forceinline__ int64_t count2(int64_t m, int64_t nA, int64_t nB)
+{
+    // #(A, B) in [0,nA) x [0,nB) with A + B = m
+    if (m < 0 || m > nA - 1 + nB - 1) return 0;
+    const int64_t lo = m - (nB - 1) > 0 ? m - (nB - 1) : 0;
+    const int64_t hi = m < nA - 1 ? m : nA - 1;
+    return hi - lo + 1;
+}
+
+template <int DIM>
+__device__ void decode_tile(int64_t tk, const int64_t* __restrict__ pre, const WaveGeo& wg, int64_t& b, int64_t& I,
+                            int64_t& J, int64_t& K)
+{
+    int64_t lo = 0, hi = wg.nD - 1;  // largest d with pre[d] <= tk
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (pre[mid] <= tk) lo = mid; else hi = mid - 1;
+    }
+    const int64_t d = lo;
+    int64_t r = tk - pre[d];
+    b = I = J = K = 0;
+    for (int64_t bb = 0; bb < wg.nB; ++bb) {
+        const int64_t m = d - bb * wg.db;
+        if (m < 0) break;
+        if (DIM == 2) {
+            const int64_t cnt = count2(m, wg.nI, wg.nJ);
+            if (r < cnt) {
+                b = bb;
+                I = (m - (wg.nJ - 1) > 0 ? m - (wg.nJ - 1) : 0) + r;
+                J = m - I;
+                return;
+            }
+            r -= cnt;
+        } else {
+            for (int64_t ii = 0; ii < wg.nI && ii <= m; ++ii) {
+                const int64_t cnt = count2(m - ii, wg.nJ, wg.nK);
+                if (r < cnt) {
+                    b = bb;
+                    I = ii;
+                    J = ((m - ii) - (wg.nK - 1) > 0 ? (m - ii) - (wg.nK - 1) : 0) + r;
+                    K = m - ii - J;
+                    return;
+                }
+                r -= cnt;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ bool wait_flag(const int* f, int tag, int spin)
+{
+    for (int it = 0; it < spin; ++it) {
+        if (ld_acquire(f) == tag) return true;
+        __nanosleep(500);
+    }
+    return false;
+}
+
+// Which window cells a point update reads: every cell for a box; for a star
+// the centre row in full and the other rows only above/below the points.
+template <int SHAPE, int R, int W>
+__host__ __device__ constexpr bool needed(int r0, int r1, int cc)
+{
+    return SHAPE == BOX || (r0 == 0 && r1 == 0) || ((r0 == 0 || r1 == 0) && cc >= R && cc < W + R);
+}
+
+// One step of one lane: W points along the fast axis starting at (p0, p1, p2).
+// The window of neighbour values is loaded first (nothing this step writes is
+// read through it except the same-row left values, which come from regs).
+template <int DIM, int SHAPE, int R, int ARITH, int W>
+__device__ __forceinline__ void lane_step(double* __restrict__ u, const Geo& g, double c, const double* w, int64_t p0,
+                                          int64_t p1, int64_t p2)
+{
+    using St = Stn<DIM, SHAPE, R>;
+    constexpr int NR0 = DIM == 3 ? 2 * R + 1 : 1;
+    constexpr int NR1 = 2 * R + 1;
+    constexpr int NC = W + 2 * R;
+    double win[NR0][NR1][NC];
+#pragma unroll
+    for (int a = 0; a < NR0; ++a)
+#pragma unroll
+        for (int bq = 0; bq < NR1; ++bq)
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) {
+                const int r0 = DIM == 3 ? a - R : 0;
+                const int r1 = bq - R;
+                if (needed<SHAPE, R, W>(r0, r1, cc)) {
+                    const int64_t q0 = p0 + r0, q1 = p1 + r1, q2 = p2 + cc - R;
+                    const bool in = q0 >= 0 && q0 < g.n0 && q1 >= 0 && q1 < g.n1 && q2 >= 0 && q2 < g.n2;
+                    win[a][bq][cc] = in ? __ldcg(u + (q0 * g.n1 + q1) * g.n2 + q2) : c;
+                }
+            }
+#pragma unroll
+    for (int m = 0; m < W; ++m) {
+        const int64_t q2 = p2 + m;
+        double v[St::K];
+#pragma unroll
+        for (int q = 0; q < St::K; ++q) {
+            const int o0 = St::o(q, 0), o1 = St::o(q, 1), o2 = St::o(q, 2);
+            v[q] = win[DIM == 3 ? o0 + R : 0][o1 + R][m + o2 + R];
+        }
+        double acc = __dmul_rn(w[0], v[0]);
+#pragma unroll
+        for (int q = 1; q < St::K; ++q) acc = acc_step<ARITH>(acc, w[q], v[q]);
+        if (q2 >= 0 && q2 < g.n2) {
+            u[(p0 * g.n1 + p1) * g.n2 + q2] = acc;
+            win[DIM == 3 ? R : 0][R][m + R] = acc;  // newest value, read by the next points as a left neighbour
+        }
+    }
+}
+
+template <int DIM, int SHAPE, int R, int ARITH, int W>
+__global__ void __launch_bounds__(128) k_gs_wave(double* __restrict__ u, Geo g, double c,
+                                                 WArr<Stn<DIM, SHAPE, R>::K> w, WaveGeo wg,
+                                                 const int64_t* __restrict__ pre, int* __restrict__ flags,
+                                                 int* __restrict__ ticket, int* status, int tag, WaitCfg wc)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int64_t tk = 0;
+        if (lane == 0) tk = atomicAdd((unsigned long long*)ticket, 1ull);
+        tk = __shfl_sync(FULL, tk, 0);
+        if (tk >= wg.ntiles) return;
+        int64_t b, I, J, K;
+        decode_tile<DIM>(tk, pre, wg, b, I, J, K);
+        const int64_t fidx = ((b * wg.nI + I) * wg.nJ + J) * wg.nK + K;
+        // predecessors: the three lower neighbours in this block, the shifted tile of the previous block
+        bool ok = true;
+        if (I > 0) ok &= wait_flag(flags + fidx - wg.nJ * wg.nK, tag, wc.spin);
+        if (J > 0) ok &= wait_flag(flags + fidx - wg.nK, tag, wc.spin);
+        if (K > 0) ok &= wait_flag(flags + fidx - 1, tag, wc.spin);
+        if (b > 0) {
+            const int64_t pI = I + wg.dI < wg.nI - 1 ? I + wg.dI : wg.nI - 1;
+            const int64_t pJ = J + wg.dJ < wg.nJ - 1 ? J + wg.dJ : wg.nJ - 1;
+            const int64_t pK = K + wg.dK < wg.nK - 1 ? K + wg.dK : wg.nK - 1;
+            ok &= wait_flag(flags + (((b - 1) * wg.nI + pI) * wg.nJ + pJ) * wg.nK + pK, tag, wc.spin);
+        }
+        if (!ok && lane == 0) atomicExch(status, DEV_TIMEOUT);
+        __syncwarp();
+        const int64_t L = wg.T - 32 * b < 32 ? wg.T - 32 * b : 32;
+        const bool active = ok && lane < L;
+        const int nsteps = DIM == 3 ? wg.H * wg.HJ : wg.H;
+        for (int st = 0; st < nsteps; ++st) {
+            if (active) {
+                if (DIM == 2) {
+                    const int64_t i2 = I * wg.H + st;
+                    const int64_t p1 = i2 - (int64_t)wg.s * lane;
+                    if (p1 >= 0 && p1 < g.n1) {
+                        const int64_t p2 = J * W - (int64_t)wg.a1 * p1 - (int64_t)wg.b1 * lane;
+                        if (p2 + W > 0 && p2 < g.n2) lane_step<DIM, SHAPE, R, ARITH, W>(u, g, c, w.w, 0, p1, p2);
+                    }
+                } else {
+                    const int64_t i2 = I * wg.H + st / wg.HJ;
+                    const int64_t j2 = J * wg.HJ + st % wg.HJ;
+                    const int64_t p0 = i2 - (int64_t)wg.s * lane;
+                    if (p0 >= 0 && p0 < g.n0) {
+                        const int64_t p1 = j2 - (int64_t)wg.a1 * p0 - (int64_t)wg.b1 * lane;
+                        if (p1 >= 0 && p1 < g.n1) {
+                            const int64_t p2 = K * W - (int64_t)wg.a2 * p0 - (int64_t)wg.c2 * p1 - (int64_t)wg.b2 * lane;
+                            if (p2 + W > 0 && p2 < g.n2) lane_step<DIM, SHAPE, R, ARITH, W>(u, g, c, w.w, p0, p1, p2);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (lane == 0 && fidx != wc.stall) {
+            __threadfence();
+            st_release(flags + fidx, tag);
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------- host ---
+
+bool gs_wavefront_supported(const stencil_handle_s* h, const Geo& g)
+{
+    (void)g;
+    if (h->method != GAUSS_SEIDEL || h->bc != BC_CONSTANT) return false;
+    if (h->dim == 1) return h->r >= 1 && h->r <= 4;
+    if (h->dim == 2) return h->r <= 2;
+    return h->r == 1;
+}
+
+// Grow the handle's wavefront workspace to at least bytes (zeroed when grown).
+static int wave_workspace(stencil_handle_s* h, size_t bytes, cudaStream_t st)
+{
+    if (h->wave_ws_bytes >= bytes) return STENCIL_OK;
+    if (h->wave_ws) {
+        cudaStreamSynchronize(st);
+        cudaFree(h->wave_ws);
+        h->wave_ws = nullptr;
+        h->wave_ws_bytes = 0;
+    }
+    size_t want = bytes + bytes / 4 + 4096;
+    if (cudaMalloc(&h->wave_ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        return STENCIL_ENOMEM;
+    }
+    if (cudaMemset(h->wave_ws, 0, want) != cudaSuccess) return STENCIL_ECUDA;
+    h->wave_ws_bytes = want;
+    h->wave_epoch = 0;
+    return STENCIL_OK;
+}
+
+static WaitCfg take_wait_cfg(stencil_handle_s* h)
+{
+    WaitCfg wc{h->debug_spin > 0 ? h->debug_spin : SPIN_LIMIT, h->debug_stall_tile};
+    h->debug_stall_tile = -1;
+    h->debug_spin = 0;
+    return wc;
+}
+
+template <int R>
+static int wave_1d(const RunCtx& ctx, double* u, int64_t T)
+{
+    stencil_handle_s* h = ctx.h;
+    WArr<2 * R + 1> w;
+    for (int q = 0; q < 2 * R + 1; ++q) w.w[q] = h->w_desc[q];
+    const int64_t nB = (T + 31) / 32;
+    const size_t bytes = 64 + (size_t)nB * sizeof(unsigned long long);
+    int rc = wave_workspace(h, bytes, ctx.st);
+    if (rc) return rc;
+    int* ticket = (int*)h->wave_ws;
+    unsigned long long* progress = (unsigned long long*)((char*)h->wave_ws + 64);
+    const unsigned tag = (unsigned)(++h->wave_epoch) & 0xffffffu;
+    if (cudaMemsetAsync(ticket, 0, sizeof(int), ctx.st) != cudaSuccess) return STENCIL_ECUDA;
+    const WaitCfg wc = take_wait_cfg(h);
+    if (h->arith == ARITH_FMA)
+        k_gs1d_wave<R, ARITH_FMA><<<(unsigned)nB, 32, 0, ctx.st>>>(u, ctx.g.n2, h->c, w, T, progress, ticket,
+                                                                     h->d_status, tag, wc);
+    else
+        k_gs1d_wave<R, ARITH_UNFUSED><<<(unsigned)nB, 32, 0, ctx.st>>>(u, ctx.g.n2, h->c, w, T, progress, ticket,
+                                                                         h->d_status, tag, wc);
+    g_launches++;
+    return cuda_rc(cudaGetLastError());
+}
+
+template <int DIM, int SHAPE, int R, int W>
+static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes)
+{
+    (void)lanes;
+    stencil_handle_s* h = ctx.h;
+    constexpr int K = Stn<DIM, SHAPE, R>::K;
+    WArr<K> w;
+    for (int q = 0; q < K; ++q) w.w[q] = h->w_desc[q];
+    const Geo& g = ctx.g;
+    const bool box = SHAPE == BOX;
+    WaveGeo wg;
+    wg.s = R + 1;
+    if (DIM == 2) {
+        wg.a1 = box ? R : 0;
+        wg.b1 = R * (1 + wg.a1);
+        wg.a2 = wg.c2 = wg.b2 = 0;
+        wg.H = 16;
+        wg.HJ = 1;
+    } else {
+        wg.a1 = box ? R : 0;
+        wg.b1 = R * (1 + wg.a1);
+        wg.c2 = box ? R : 0;
+        wg.a2 = box ? R * (1 + R) : 0;
+        wg.b2 = R * (1 + wg.a2 + wg.c2);
+        wg.H = 4;
+        wg.HJ = 4;
+    }
+    const int64_t L = 32;
+    int64_t extI, extJ, extK;
+    if (DIM == 2) {
+        extI = g.n1 + wg.s * (L - 1);
+        extJ = g.n2 + wg.a1 * (g.n1 - 1) + wg.b1 * (L - 1);
+        wg.nI = (extI + wg.H - 1) / wg.H;
+        wg.nJ = (extJ + W - 1) / W;
+        wg.nK = 1;
+        wg.dI = (R + wg.s * (int)(L - 1)) / wg.H + 2;
+        wg.dJ = (R * (1 + wg.a1) + wg.b1 * (int)(L - 1)) / W + 2;
+        wg.dK = 0;
+    } else {
+        extI = g.n0 + wg.s * (L - 1);
+        extJ = g.n1 + wg.a1 * (g.n0 - 1) + wg.b1 * (L - 1);
+        extK = g.n2 + wg.a2 * (g.n0 - 1) + wg.c2 * (g.n1 - 1) + wg.b2 * (L - 1);
+        wg.nI = (extI + wg.H - 1) / wg.H;
+        wg.nJ = (extJ + wg.HJ - 1) / wg.HJ;
+        wg.nK = (extK + W - 1) / W;
+        wg.dI = (R + wg.s * (int)(L - 1)) / wg.H + 2;
+        wg.dJ = (R * (1 + wg.a1) + wg.b1 * (int)(L - 1)) / wg.HJ + 2;
+        wg.dK = (R * (1 + wg.a2 + wg.c2) + wg.b2 * (int)(L - 1)) / W + 2;
+    }
+    wg.nB = (T + 31) / 32;
+    wg.T = T;
+    wg.db = wg.dI + wg.dJ + wg.dK + 1;
+    wg.nD = (wg.nI - 1) + (wg.nJ - 1) + (wg.nK - 1) + (wg.nB - 1) * wg.db + 1;
+    wg.ntiles = wg.nB * wg.nI * wg.nJ * wg.nK;
+    if (wg.ntiles > (int64_t)1 << 31) return STENCIL_EUNSUPPORTED;
+    // tiles per diagonal, then prefix sums
+    std::vector<int64_t> pre((size_t)wg.nD + 1, 0);
+    for (int64_t b = 0; b < wg.nB; ++b)
+        for (int64_t I = 0; I < wg.nI; ++I)
+            for (int64_t J = 0; J < wg.nJ; ++J) {
+                const int64_t d0 = I + J + b * wg.db;
+                for (int64_t Kt = 0; Kt < wg.nK; ++Kt) pre[(size_t)(d0 + Kt) + 1]++;
+            }
+    for (int64_t d = 0; d < wg.nD; ++d) pre[(size_t)d + 1] += pre[(size_t)d];
+    const size_t pre_bytes = pre.size() * sizeof(int64_t);
+    const size_t flag_off = 256 + ((pre_bytes + 255) & ~size_t(255));
+    const size_t bytes = flag_off + (size_t)wg.ntiles * sizeof(int);
+    int rc = wave_workspace(h, bytes, ctx.st);
+    if (rc) return rc;
+    int* ticket = (int*)h->wave_ws;  // 8 bytes used (64-bit counter)
+    int64_t* dpre = (int64_t*)((char*)h->wave_ws + 256);
+    int* flags = (int*)((char*)h->wave_ws + flag_off);
+    const int tag = (++h->wave_epoch) & 0x3fffffff;
+    if (cudaMemsetAsync(ticket, 0, 8, ctx.st) != cudaSuccess) return STENCIL_ECUDA;
+    if (cudaMemcpyAsync(dpre, pre.data(), pre_bytes, cudaMemcpyHostToDevice, ctx.st) != cudaSuccess)
+        return STENCIL_ECUDA;
+    // the table is read by the kernel; keep the host copy alive until the copy has run
+    if (cudaStreamSynchronize(ctx.st) != cudaSuccess) return STENCIL_ECUDA;
+    auto kern = h->arith == ARITH_FMA ? k_gs_wave<DIM, SHAPE, R, ARITH_FMA, W> : k_gs_wave<DIM, SHAPE, R, ARITH_UNFUSED, W>;
+    int nsm = 0, per_sm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
+    int64_t nblk = (int64_t)nsm * (per_sm > 4 ? 4 : (per_sm > 0 ? per_sm : 1));
+    const int64_t need = (wg.ntiles + 3) / 4;
+    if (nblk > need) nblk = need;
+    const WaitCfg wc = take_wait_cfg(h);
+    kern<<<(unsigned)nblk, 128, 0, ctx.st>>>(u, g, h->c, w, wg, dpre, flags, ticket, h->d_status, tag, wc);
+    g_launches++;
+    return cuda_rc(cudaGetLastError());
+}
+
+int gs_wavefront_run(const RunCtx& ctx, double* u, int64_t T, int lanes)
+{
+    const stencil_handle_s* h = ctx.h;
+    if (h->dim == 1) {
+        switch (h->r) {
+            case 1: return wave_1d<1>(ctx, u, T);
+            case 2: return wave_1d<2>(ctx, u, T);
+            case 3: return wave_1d<3>(ctx, u, T);
+            case 4: return wave_1d<4>(ctx, u, T);
+        }
+        return STENCIL_EUNSUPPORTED;
+    }
+    if (h->dim == 2) {
+        if (h->shape == STAR && h->r == 1) return wave_tiles<2, STAR, 1, 16>(ctx, u, T, lanes);
+        if (h->shape == BOX && h->r == 1) return wave_tiles<2, BOX, 1, 16>(ctx, u, T, lanes);
+        if (h->shape == STAR && h->r == 2) return wave_tiles<2, STAR, 2, 8>(ctx, u, T, lanes);
+        if (h->shape == BOX && h->r == 2) return wave_tiles<2, BOX, 2, 8>(ctx, u, T, lanes);
+    } else {
+        if (h->shape == STAR && h->r == 1) return wave_tiles<3, STAR, 1, 8>(ctx, u, T, lanes);
+        if (h->shape == BOX && h->r == 1) return wave_tiles<3, BOX, 1, 4>(ctx, u, T, lanes);
+    }
+    return STENCIL_EUNSUPPORTED;
+}
+
 }  // namespace gbst

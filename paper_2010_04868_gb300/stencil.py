@@ -30,7 +30,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgb300ste
 #: Every entry point that include/stencil.h declares.
 EXPORTS = ("stencil_create", "stencil_set_plan", "stencil_run", "stencil_run_batch", "stencil_workspace_bytes",
            "stencil_status", "stencil_destroy", "stencil_strerror", "stencil_run_host", "stencil_launch_count",
-           "stencil_run_noalloc")
+           "stencil_run_noalloc", "stencil_debug_inject_stall")
 
 #: Largest grid (points) stencil_run_noalloc accepts: its fixed workspace holds 2^21 doubles.
 NOALLOC_MAX_POINTS = 1 << 21
@@ -63,6 +63,7 @@ def load(path: str = LIB_PATH):
     lib.stencil_strerror.restype = ctypes.c_char_p
     lib.stencil_run_host.argtypes = [P, P, ctypes.POINTER(I64), P, P, I64, P]
     lib.stencil_run_noalloc.argtypes = [P, ctypes.POINTER(stencil_grid), I64, P]
+    lib.stencil_debug_inject_stall.argtypes = [P, I64, I]
     lib.stencil_launch_count.argtypes = []
     lib.stencil_launch_count.restype = ctypes.c_uint64
     for name in EXPORTS:
@@ -156,6 +157,11 @@ def stencil_run_noalloc(h, grid: stencil_grid, T, stream_ptr=None):
         raise StencilError(rc, "stencil_run_noalloc: grid of %d points exceeds the %d-point no-allocation "
                                "workspace (or the handle is not supported)" % (npts, NOALLOC_MAX_POINTS))
     return check(rc, "stencil_run_noalloc")
+
+
+def stencil_debug_inject_stall(h, unit, spin=0):
+    """Failure-detection test hook: the next wavefront run never publishes work unit `unit`."""
+    return check(load().stencil_debug_inject_stall(h, int(unit), int(spin)), "stencil_debug_inject_stall")
 
 
 def stencil_launch_count() -> int:

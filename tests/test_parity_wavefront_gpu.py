@@ -1,0 +1,103 @@
+"""Parity of the time-skewed wavefront Gauss-Seidel kernel with the oracle, bit for bit."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from helpers import bits_equal, case, first_diff, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+WAVE = 3
+PLAIN = 1
+
+CASES_1D = [((1,), 1), ((37,), 1), ((1000,), 1), ((4099,), 1), ((300,), 2), ((101,), 3), ((64,), 4), ((3,), 1)]
+
+
+@pytest.mark.parametrize("ext,r", CASES_1D)
+@pytest.mark.parametrize("c", [0.0, 0.4])
+def test_gs1d_wavefront(ext, r, c):
+    w, u0 = case(1, "star", r, ext, seed=r + 60)
+    for T in (1, 5, 31, 32, 33, 64, 97):
+        for arith in ("fma", "unfused"):
+            ref = oracle_run(u0, T, 1, "star", r, w, "gs", "constant", c, arith)
+            got = gpu_run(u0, T, 1, "star", r, w, "gs", "constant", c, arith, plan=WAVE)
+            assert bits_equal(got, ref), (T, arith, first_diff(got, ref))
+
+
+CASES_ND = [
+    (2, "star", 1, (1, 1)), (2, "star", 1, (37, 130)), (2, "star", 1, (130, 37)), (2, "box", 1, (70, 131)),
+    (2, "star", 2, (64, 65)), (2, "box", 2, (33, 70)),
+    (3, "star", 1, (5, 6, 7)), (3, "star", 1, (20, 17, 40)), (3, "box", 1, (9, 10, 21)),
+]
+
+
+@pytest.mark.parametrize("dim,shape,r,ext", CASES_ND)
+@pytest.mark.parametrize("c", [0.0, 0.4])
+def test_gs_nd_wavefront(dim, shape, r, ext, c):
+    w, u0 = case(dim, shape, r, ext, seed=dim * 10 + r + 70)
+    for T in (1, 7, 32, 45):
+        for arith in ("fma", "unfused"):
+            ref = oracle_run(u0, T, dim, shape, r, w, "gs", "constant", c, arith)
+            got = gpu_run(u0, T, dim, shape, r, w, "gs", "constant", c, arith, plan=WAVE)
+            assert bits_equal(got, ref), (T, arith, first_diff(got, ref))
+
+
+def test_gs2d_full_size_wavefront_equals_oracle():
+    """The 4096^2 Gauss-Seidel 5-point workload in its launch configuration, T cut to 24 for the serial oracle."""
+    from paper_2010_04868_gb300 import inputs
+    u0 = inputs.grid(inputs.SEED_BASE + 3, (4096, 4096))
+    w = inputs.normalized_weights(inputs.SEED_BASE + 105, 5)
+    ref = oracle_run(u0, 24, 2, "star", 1, w, "gs", "constant", 0.0, "fma")
+    got = gpu_run(u0, 24, 2, "star", 1, w, "gs", "constant", 0.0, "fma", plan=WAVE)
+    assert bits_equal(got, ref), first_diff(got, ref)
+
+
+def test_gs2d_full_size_full_T_wavefront_equals_plain():
+    """Full 4096^2 x 200 sweeps: wavefront and plain sweep kernels agree bit for bit."""
+    from paper_2010_04868_gb300 import inputs
+    u0 = inputs.grid(inputs.SEED_BASE + 3, (4096, 4096))
+    w = inputs.normalized_weights(inputs.SEED_BASE + 105, 5)
+    a = gpu_run(u0, 200, 2, "star", 1, w, "gs", "constant", 0.0, "fma", plan=WAVE)
+    b = gpu_run(u0, 200, 2, "star", 1, w, "gs", "constant", 0.0, "fma", plan=PLAIN)
+    assert bits_equal(a, b), first_diff(a, b)
+
+
+def test_gs1d_long_wavefront_equals_oracle():
+    """The 1D Gauss-Seidel workload at its full N = 2^24, T cut to 40 for the serial oracle."""
+    from paper_2010_04868_gb300 import inputs
+    u0 = inputs.grid(inputs.SEED_BASE + 4, (1 << 24,))
+    w = inputs.normalized_weights(inputs.SEED_BASE + 103, 3)
+    ref = oracle_run(u0, 40, 1, "star", 1, w, "gs", "constant", 0.0, "fma")
+    got = gpu_run(u0, 40, 1, "star", 1, w, "gs", "constant", 0.0, "fma", plan=WAVE)
+    assert bits_equal(got, ref), first_diff(got, ref)
+
+
+@pytest.mark.parametrize("dim,ext,unit", [(1, (5000,), 0), (2, (40, 50), 3), (3, (8, 9, 10), 5)])
+def test_stalled_producer_times_out_without_hanging(dim, ext, unit):
+    """A producer that never publishes makes its consumers' bounded waits expire: ETIMEOUT, no hang."""
+    import torch
+    from paper_2010_04868_gb300 import stencil as S
+    w, u0 = case(dim, "star", 1, ext, seed=5)
+    st = S.Stencil(dim, 0, 1, list(w), S.STENCIL_GAUSS_SEIDEL).set_plan(WAVE)
+    u = torch.from_numpy(u0.copy()).cuda()
+    S.stencil_debug_inject_stall(st.handle, unit, 20000)
+    st.run(u, 70)
+    assert st.status() == S.STENCIL_ETIMEOUT
+    # the handle and the context stay usable: the next run is correct again
+    u.copy_(torch.from_numpy(u0))
+    st.run(u, 70)
+    assert st.status() == 0
+    ref = oracle_run(u0, 70, dim, "star", 1, w, "gs", "constant", 0.0, "fma")
+    assert bits_equal(u.cpu().numpy(), ref)
+    st.close()
+
+
+def test_periodic_wavefront_is_rejected():
+    import torch
+    from paper_2010_04868_gb300 import stencil as S
+    st = S.Stencil(2, 0, 1, [0.2] * 5, S.STENCIL_GAUSS_SEIDEL, S.STENCIL_BC_PERIODIC).set_plan(WAVE)
+    with pytest.raises(S.StencilError) as e:
+        st.run(torch.zeros(8, 8, dtype=torch.float64, device="cuda"), 3)
+    assert e.value.code == S.STENCIL_EUNSUPPORTED
+    st.close()
