@@ -124,10 +124,18 @@ int stencil_run(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_s
 
 /*
  * Run n independent problems (h[i], g[i], T[i]) with as few launches as
- * possible: the Jacobi steps of every problem are walked by one persistent
- * kernel per pass over a shared work list, replayed from a CUDA graph that
- * is cached on the batch's shape. Every g[i] needs its scratch set. The
- * results equal n separate stencil_run calls bit for bit.
+ * possible. One persistent kernel walks a shared work list: the time steps
+ * (or T_b-step blocked passes, as each problem's tuned plan says) of every
+ * Jacobi problem and the tile diagonals of every Gauss-Seidel sweep, a unit
+ * starting once its problem's previous phase is done. Gauss-Seidel problems
+ * whose plan is the wavefront kernel run as their own launches on the same
+ * stream. The work of a batch shape (handles, pointers, extents, T, plans) is
+ * prepared and captured into a CUDA graph on first use and replayed on later
+ * calls with the same shape. Every Jacobi g[i] needs its scratch set. The
+ * results equal n separate stencil_run calls bit for bit. Inside a stream
+ * capture that the caller runs, only a batch shape already run once outside
+ * capture is accepted (its prepared work is enqueued without allocating);
+ * a new shape there returns STENCIL_EUNSUPPORTED.
  */
 int stencil_run_batch(const stencil_handle* h, const stencil_grid* g, const int64_t* T, int n,
                       void* cuda_stream);

@@ -150,7 +150,7 @@ int stencil_run(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_s
     const size_t bytes = (size_t)npoints(h->dim, g->ext) * sizeof(double);
 
     if (h->method == STENCIL_GAUSS_SEIDEL) {
-        Plan p = plan_for(h, ctx.g, T);
+        Plan p = plan_for(h, ctx.g, T, ctx.st);
         if (p.kernel == STENCIL_KERNEL_WAVEFRONT) {
             if (!gs_wavefront_supported(h, ctx.g)) return STENCIL_EUNSUPPORTED;
             return gs_wavefront_run(ctx, g->data, T, p.tb);
@@ -169,7 +169,7 @@ int stencil_run(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_s
     } else if (scratch == g->data) {
         return STENCIL_EINVAL;
     }
-    Plan p = plan_for(h, ctx.g, T);
+    Plan p = plan_for(h, ctx.g, T, ctx.st);
     if (p.kernel == STENCIL_KERNEL_BLOCKED) {
         if (!jacobi_blocked_supported(h, ctx.g))
             rc = STENCIL_EUNSUPPORTED;

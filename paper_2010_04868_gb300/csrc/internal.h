@@ -61,6 +61,8 @@ bool jacobi_blocked_supported(const stencil_handle_s* h, const Geo& g);
 
 // Time-skewed wavefront Gauss-Seidel: T sweeps in place.
 int gs_wavefront_run(const RunCtx& ctx, double* u, int64_t T, int lanes);
+// Size the handle's wavefront workspace for (g, T) ahead of a captured run.
+int gs_wavefront_prepare(stencil_handle_s* h, const Geo& g, int64_t T);
 bool gs_wavefront_supported(const stencil_handle_s* h, const Geo& g);
 
 // Geometry from a stencil_grid (padded to three dimensions).

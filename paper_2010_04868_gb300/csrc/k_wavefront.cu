@@ -119,17 +119,30 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
     const unsigned long long mytag = (unsigned long long)tag << PROG_SHIFT;
     int64_t known = b > 0 ? 0 : INT64_MAX;
 
+    // Lane 0's previous-sweep values (the "bottom vector") arrive in chunks of
+    // 32 positions, loaded by the whole warp one chunk ahead of use and handed
+    // to lane 0 by shuffle, so no load latency sits on the step's critical path.
+    auto need_upto = [&](int64_t upto) {
+        // positions [0, upto) must be final in the previous block's output
+        if (lane == 0 && upto > known) known = wait_progress(prev, upto, tag, status, wc.spin);
+        __syncwarp();
+    };
+    auto load_chunk = [&](int64_t ch) -> double {
+        const int64_t p = ch * 32 + lane;
+        return (p >= 0 && p < n) ? __ldcg(u + p) : c;
+    };
+    int64_t cur_ch = 0;
+    need_upto(n < 64 ? n : 64);
+    double cur = load_chunk(0), nxt = load_chunk(1);
+
     // old[o]: previous-sweep value at x - 1 + o (before the step's receive);
     // nw[a]: this sweep's value at x - 1 - a
     double old[R + 1], nw[R];
 #pragma unroll
     for (int o = 0; o <= R; ++o) {
-        const int64_t p = -1 + o;
-        old[o] = c;
-        if (lane == 0 && p >= 0 && p < n) {
-            if (p >= known) known = wait_progress(prev, p + 1, tag, status, wc.spin);
-            old[o] = __ldcg(u + p);
-        }
+        const int64_t p = -1 + o;  // < 32: inside chunk 0
+        const double v = __shfl_sync(FULL, cur, (int)(p >= 0 ? p : 0));
+        old[o] = (lane == 0 && p >= 0 && p < n) ? v : c;
     }
 #pragma unroll
     for (int a = 0; a < R; ++a) nw[a] = c;
@@ -137,16 +150,17 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
     const int64_t steps = n + (int64_t)S * (L - 1);
     for (int64_t step = 0; step < steps; ++step) {
         const int64_t x = step - (int64_t)S * lane;
-        double recv = __shfl_up_sync(FULL, out, 1);
-        if (lane == 0) {
-            const int64_t p = x + R;
-            recv = c;
-            if (p < n) {
-                // wait for a chunk ahead so the next waits are rare; never past the grid end
-                if (p >= known) known = wait_progress(prev, (p + 257 < n ? p + 257 : n), tag, status, wc.spin);
-                recv = __ldcg(u + p);
-            }
+        const int64_t p = step + R;  // lane 0's newest previous-sweep position
+        if ((p >> 5) != cur_ch) {
+            cur_ch = p >> 5;
+            cur = nxt;
+            const int64_t upto = (cur_ch + 2) * 32;
+            need_upto(upto < n ? upto : n);
+            nxt = load_chunk(cur_ch + 1);
         }
+        const double bottom = __shfl_sync(FULL, cur, (int)(p & 31));
+        double recv = __shfl_up_sync(FULL, out, 1);
+        if (lane == 0) recv = p < n ? bottom : c;
 #pragma unroll
         for (int o = 0; o < R; ++o) old[o] = old[o + 1];
         old[R] = recv;
@@ -359,6 +373,31 @@ __global__ void __launch_bounds__(128) k_gs_wave(double* __restrict__ u, Geo g, 
     }
 }
 
+// Schedule table: pre[d] = number of tiles on diagonals before d (tiles on
+// diagonal d: b*db + I + J + K = d). Counts in parallel, prefix sum by one thread.
+template <int DIM>
+__global__ void k_wave_prefix(WaveGeo wg, int64_t* pre)
+{
+    for (int64_t d = threadIdx.x; d < wg.nD; d += blockDim.x) {
+        int64_t cnt = 0;
+        for (int64_t b = 0; b < wg.nB; ++b) {
+            const int64_t m = d - b * wg.db;
+            if (m < 0) break;
+            if (DIM == 2) {
+                cnt += count2(m, wg.nI, wg.nJ);
+            } else {
+                for (int64_t ii = 0; ii < wg.nI && ii <= m; ++ii) cnt += count2(m - ii, wg.nJ, wg.nK);
+            }
+        }
+        pre[d + 1] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        pre[0] = 0;
+        for (int64_t d = 0; d < wg.nD; ++d) pre[d + 1] += pre[d];
+    }
+}
+
 // ------------------------------------------------------------------- host ---
 
 bool gs_wavefront_supported(const stencil_handle_s* h, const Geo& g)
@@ -374,8 +413,9 @@ bool gs_wavefront_supported(const stencil_handle_s* h, const Geo& g)
 static int wave_workspace(stencil_handle_s* h, size_t bytes, cudaStream_t st)
 {
     if (h->wave_ws_bytes >= bytes) return STENCIL_OK;
+    (void)st;
     if (h->wave_ws) {
-        cudaStreamSynchronize(st);
+        cudaDeviceSynchronize();
         cudaFree(h->wave_ws);
         h->wave_ws = nullptr;
         h->wave_ws_bytes = 0;
@@ -400,7 +440,7 @@ static WaitCfg take_wait_cfg(stencil_handle_s* h)
 }
 
 template <int R>
-static int wave_1d(const RunCtx& ctx, double* u, int64_t T)
+static int wave_1d(const RunCtx& ctx, double* u, int64_t T, bool prepare_only = false)
 {
     stencil_handle_s* h = ctx.h;
     WArr<2 * R + 1> w;
@@ -408,11 +448,12 @@ static int wave_1d(const RunCtx& ctx, double* u, int64_t T)
     const int64_t nB = (T + 31) / 32;
     const size_t bytes = 64 + (size_t)nB * sizeof(unsigned long long);
     int rc = wave_workspace(h, bytes, ctx.st);
-    if (rc) return rc;
+    if (rc || prepare_only) return rc;
     int* ticket = (int*)h->wave_ws;
     unsigned long long* progress = (unsigned long long*)((char*)h->wave_ws + 64);
-    const unsigned tag = (unsigned)(++h->wave_epoch) & 0xffffffu;
-    if (cudaMemsetAsync(ticket, 0, sizeof(int), ctx.st) != cudaSuccess) return STENCIL_ECUDA;
+    // stream-ordered reset of the ticket and progress words: replays of a captured graph start clean
+    const unsigned tag = 1;
+    if (cudaMemsetAsync(h->wave_ws, 0, bytes, ctx.st) != cudaSuccess) return STENCIL_ECUDA;
     const WaitCfg wc = take_wait_cfg(h);
     if (h->arith == ARITH_FMA)
         k_gs1d_wave<R, ARITH_FMA><<<(unsigned)nB, 32, 0, ctx.st>>>(u, ctx.g.n2, h->c, w, T, progress, ticket,
@@ -425,7 +466,7 @@ static int wave_1d(const RunCtx& ctx, double* u, int64_t T)
 }
 
 template <int DIM, int SHAPE, int R, int W>
-static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes)
+static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes, bool prepare_only = false)
 {
     (void)lanes;
     stencil_handle_s* h = ctx.h;
@@ -479,29 +520,21 @@ static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes)
     wg.nD = (wg.nI - 1) + (wg.nJ - 1) + (wg.nK - 1) + (wg.nB - 1) * wg.db + 1;
     wg.ntiles = wg.nB * wg.nI * wg.nJ * wg.nK;
     if (wg.ntiles > (int64_t)1 << 31) return STENCIL_EUNSUPPORTED;
-    // tiles per diagonal, then prefix sums
-    std::vector<int64_t> pre((size_t)wg.nD + 1, 0);
-    for (int64_t b = 0; b < wg.nB; ++b)
-        for (int64_t I = 0; I < wg.nI; ++I)
-            for (int64_t J = 0; J < wg.nJ; ++J) {
-                const int64_t d0 = I + J + b * wg.db;
-                for (int64_t Kt = 0; Kt < wg.nK; ++Kt) pre[(size_t)(d0 + Kt) + 1]++;
-            }
-    for (int64_t d = 0; d < wg.nD; ++d) pre[(size_t)d + 1] += pre[(size_t)d];
-    const size_t pre_bytes = pre.size() * sizeof(int64_t);
+    const size_t pre_bytes = (size_t)(wg.nD + 1) * sizeof(int64_t);
     const size_t flag_off = 256 + ((pre_bytes + 255) & ~size_t(255));
     const size_t bytes = flag_off + (size_t)wg.ntiles * sizeof(int);
     int rc = wave_workspace(h, bytes, ctx.st);
-    if (rc) return rc;
+    if (rc || prepare_only) return rc;
     int* ticket = (int*)h->wave_ws;  // 8 bytes used (64-bit counter)
     int64_t* dpre = (int64_t*)((char*)h->wave_ws + 256);
     int* flags = (int*)((char*)h->wave_ws + flag_off);
-    const int tag = (++h->wave_epoch) & 0x3fffffff;
+    // stream-ordered reset of ticket and flags, schedule table built on the device:
+    // nothing here waits on the host, so the run can be captured into a graph and replayed
+    const int tag = 1;
     if (cudaMemsetAsync(ticket, 0, 8, ctx.st) != cudaSuccess) return STENCIL_ECUDA;
-    if (cudaMemcpyAsync(dpre, pre.data(), pre_bytes, cudaMemcpyHostToDevice, ctx.st) != cudaSuccess)
-        return STENCIL_ECUDA;
-    // the table is read by the kernel; keep the host copy alive until the copy has run
-    if (cudaStreamSynchronize(ctx.st) != cudaSuccess) return STENCIL_ECUDA;
+    if (cudaMemsetAsync(flags, 0, (size_t)wg.ntiles * sizeof(int), ctx.st) != cudaSuccess) return STENCIL_ECUDA;
+    k_wave_prefix<DIM><<<1, 256, 0, ctx.st>>>(wg, dpre);
+    g_launches++;
     auto kern = h->arith == ARITH_FMA ? k_gs_wave<DIM, SHAPE, R, ARITH_FMA, W> : k_gs_wave<DIM, SHAPE, R, ARITH_UNFUSED, W>;
     int nsm = 0, per_sm = 0, dev = 0;
     cudaGetDevice(&dev);
@@ -516,28 +549,44 @@ static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes)
     return cuda_rc(cudaGetLastError());
 }
 
-int gs_wavefront_run(const RunCtx& ctx, double* u, int64_t T, int lanes)
+static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, bool prep)
 {
     const stencil_handle_s* h = ctx.h;
     if (h->dim == 1) {
         switch (h->r) {
-            case 1: return wave_1d<1>(ctx, u, T);
-            case 2: return wave_1d<2>(ctx, u, T);
-            case 3: return wave_1d<3>(ctx, u, T);
-            case 4: return wave_1d<4>(ctx, u, T);
+            case 1: return wave_1d<1>(ctx, u, T, prep);
+            case 2: return wave_1d<2>(ctx, u, T, prep);
+            case 3: return wave_1d<3>(ctx, u, T, prep);
+            case 4: return wave_1d<4>(ctx, u, T, prep);
         }
         return STENCIL_EUNSUPPORTED;
     }
     if (h->dim == 2) {
-        if (h->shape == STAR && h->r == 1) return wave_tiles<2, STAR, 1, 16>(ctx, u, T, lanes);
-        if (h->shape == BOX && h->r == 1) return wave_tiles<2, BOX, 1, 16>(ctx, u, T, lanes);
-        if (h->shape == STAR && h->r == 2) return wave_tiles<2, STAR, 2, 8>(ctx, u, T, lanes);
-        if (h->shape == BOX && h->r == 2) return wave_tiles<2, BOX, 2, 8>(ctx, u, T, lanes);
+        if (h->shape == STAR && h->r == 1) return wave_tiles<2, STAR, 1, 16>(ctx, u, T, lanes, prep);
+        if (h->shape == BOX && h->r == 1) return wave_tiles<2, BOX, 1, 16>(ctx, u, T, lanes, prep);
+        if (h->shape == STAR && h->r == 2) return wave_tiles<2, STAR, 2, 8>(ctx, u, T, lanes, prep);
+        if (h->shape == BOX && h->r == 2) return wave_tiles<2, BOX, 2, 8>(ctx, u, T, lanes, prep);
     } else {
-        if (h->shape == STAR && h->r == 1) return wave_tiles<3, STAR, 1, 8>(ctx, u, T, lanes);
-        if (h->shape == BOX && h->r == 1) return wave_tiles<3, BOX, 1, 4>(ctx, u, T, lanes);
+        if (h->shape == STAR && h->r == 1) return wave_tiles<3, STAR, 1, 8>(ctx, u, T, lanes, prep);
+        if (h->shape == BOX && h->r == 1) return wave_tiles<3, BOX, 1, 4>(ctx, u, T, lanes, prep);
     }
     return STENCIL_EUNSUPPORTED;
+}
+
+int gs_wavefront_run(const RunCtx& ctx, double* u, int64_t T, int lanes)
+{
+    return wave_dispatch(ctx, u, T, lanes, false);
+}
+
+int gs_wavefront_prepare(stencil_handle_s* h, const Geo& g, int64_t T)
+{
+    if (!gs_wavefront_supported(h, g) || T <= 0) return STENCIL_OK;
+    RunCtx ctx;
+    ctx.h = h;
+    ctx.g = g;
+    ctx.st = 0;
+    ctx.sd = StencilDev{h->K, h->r, h->bc, h->arith, h->c, h->d_w, h->d_off, h->d_status};
+    return wave_dispatch(ctx, nullptr, T, 0, true);
 }
 
 }  // namespace gbst

@@ -11,7 +11,7 @@ struct Plan {
 };
 
 // The plan a run uses: the handle's fixed plan if set, else the tuned one.
-Plan plan_for(const stencil_handle_s* h, const Geo& g, int64_t T);
+Plan plan_for(const stencil_handle_s* h, const Geo& g, int64_t T, cudaStream_t caller);
 
 // Batched execution of n problems (see stencil_run_batch).
 int batch_run(const stencil_handle* h, const stencil_grid* g, const int64_t* T, int n, cudaStream_t st);

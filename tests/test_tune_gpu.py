@@ -1,0 +1,42 @@
+"""The autotuned default plan gives the oracle's result, and the tuning cache round-trips through its file."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+from helpers import bits_equal, case, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.parametrize("dim,shape,ext,T", [(1, "star", (65536,), 256), (2, "star", (300, 200), 30),
+                                             (3, "box", (40, 30, 50), 6)])
+def test_auto_plan_matches_oracle(dim, shape, ext, T):
+    w, u0 = case(dim, shape, 1, ext, seed=81)
+    ref = oracle_run(u0, T, dim, shape, 1, w, "jacobi", "constant", 0.0, "fma")
+    got = gpu_run(u0, T, dim, shape, 1, w, "jacobi", "constant", 0.0, "fma", plan=None)
+    assert bits_equal(got, ref)
+
+
+def test_tune_cache_file(tmp_path):
+    cache = tmp_path / "tune.jsonl"
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import torch\n"
+        "from paper_2010_04868_gb300 import stencil as S\n"
+        "st = S.Stencil(1, 0, 1, [0.25, 0.5, 0.25])\n"
+        "u = torch.rand(65536, dtype=torch.float64, device='cuda')\n"
+        "st.run(u, 256); torch.cuda.synchronize(); print('ok')\n" % ROOT)
+    env = dict(os.environ, STENCIL_TUNE_CACHE=str(cache))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    lines = [json.loads(x) for x in cache.read_text().splitlines()]
+    assert len(lines) == 1 and lines[0]["kernel"] in (1, 2)
+    # a second process reads the entry instead of tuning again
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert len(cache.read_text().splitlines()) == 1
