@@ -48,26 +48,53 @@ bool plain_specialised(int dim, int shape, int r)
 
 // ---------------------------------------------------------------- Jacobi ----
 
+// Points per thread along the blocked axis (axis 1 in 2D, axis 0 in 3D): the
+// unrolled points give each thread independent FMA chains, let their loads
+// issue early and share the neighbour rows they have in common.
+template <int DIM, int K>
+__host__ __device__ constexpr int plain_rb()
+{
+    return DIM == 1 ? 1 : (DIM == 2 ? (K <= 9 ? 4 : 2) : 2);
+}
+
 template <int DIM, int SHAPE, int R, int ARITH>
 __global__ void __launch_bounds__(256) k_jacobi_plain(const double* __restrict__ u, double* __restrict__ v, Geo g,
                                                       int bc, double c, WArr<Stn<DIM, SHAPE, R>::K> w)
 {
+    constexpr int RB = plain_rb<DIM, Stn<DIM, SHAPE, R>::K>();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n2) return;
     const int64_t s1 = g.n2, s0 = g.n1 * g.n2;
     const bool kin = k >= R && k < g.n2 - R;
-    for (int64_t i = blockIdx.z; i < g.n0; i += gridDim.z) {
-        const bool iin = DIM < 3 || (i >= R && i < g.n0 - R);
-        for (int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; j < g.n1;
-             j += (int64_t)gridDim.y * blockDim.y) {
-            const bool jin = DIM < 2 || (j >= R && j < g.n1 - R);
-            const int64_t p = i * s0 + j * s1 + k;
-            double r;
-            if (kin && jin && iin)
-                r = update_interior<DIM, SHAPE, R, ARITH, true>(u, p, s0, s1, w.w);
-            else
-                r = update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w.w);
-            v[p] = r;
+    if (DIM == 3) {
+        for (int64_t i0 = (int64_t)blockIdx.z * RB; i0 < g.n0; i0 += (int64_t)gridDim.z * RB)
+            for (int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; j < g.n1;
+                 j += (int64_t)gridDim.y * blockDim.y) {
+                const bool jin = j >= R && j < g.n1 - R;
+#pragma unroll
+                for (int rb = 0; rb < RB; ++rb) {
+                    const int64_t i = i0 + rb;
+                    if (i < g.n0) {
+                        const int64_t p = i * s0 + j * s1 + k;
+                        const bool in = kin && jin && i >= R && i < g.n0 - R;
+                        v[p] = in ? update_interior<DIM, SHAPE, R, ARITH, true>(u, p, s0, s1, w.w)
+                                  : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w.w);
+                    }
+                }
+            }
+    } else {
+        for (int64_t j0 = ((int64_t)blockIdx.y * blockDim.y + threadIdx.y) * RB; j0 < g.n1;
+             j0 += (int64_t)gridDim.y * blockDim.y * RB) {
+#pragma unroll
+            for (int rb = 0; rb < RB; ++rb) {
+                const int64_t j = j0 + rb;
+                if (j < g.n1) {
+                    const int64_t p = j * s1 + k;
+                    const bool in = kin && (DIM < 2 || (j >= R && j < g.n1 - R));
+                    v[p] = in ? update_interior<DIM, SHAPE, R, ARITH, true>(u, p, s0, s1, w.w)
+                              : update_bc<DIM, SHAPE, R, ARITH>(u, 0, j, k, g, bc, c, w.w);
+                }
+            }
         }
     }
 }
@@ -86,7 +113,8 @@ __global__ void __launch_bounds__(256) k_jacobi_plain_rt(const double* __restric
 
 static void plain_launch_shape(const Geo& g, dim3& grid, dim3& block)
 {
-    int bx = 256;
+    // 3D: 64 x 4 threads, so that the j +- 1 neighbours of a point come from rows this block also reads
+    int bx = g.n0 > 1 ? 64 : 256;
     while (bx > 32 && bx / 2 >= g.n2) bx /= 2;
     block = dim3(bx, 256 / bx, 1);
     int64_t gx = (g.n2 + bx - 1) / bx;
@@ -98,10 +126,18 @@ template <int DIM, int SHAPE, int R>
 static void launch_jacobi_plain(const RunCtx& ctx, const double* in, double* out)
 {
     constexpr int K = Stn<DIM, SHAPE, R>::K;
+    constexpr int RB = plain_rb<DIM, K>();
     WArr<K> w;
     for (int q = 0; q < K; ++q) w.w[q] = ctx.h->w_desc[q];
     dim3 grid, block;
     plain_launch_shape(ctx.g, grid, block);
+    if (DIM == 3) {
+        const int64_t gz = (ctx.g.n0 + RB - 1) / RB;
+        grid.z = (unsigned)(gz < 65535 ? gz : 65535);
+    } else {
+        const int64_t gy = (ctx.g.n1 + (int64_t)block.y * RB - 1) / ((int64_t)block.y * RB);
+        grid.y = (unsigned)(gy < 65535 ? gy : 65535);
+    }
     if (ctx.h->arith == ARITH_FMA)
         k_jacobi_plain<DIM, SHAPE, R, ARITH_FMA><<<grid, block, 0, ctx.st>>>(in, out, ctx.g, ctx.h->bc, ctx.h->c, w);
     else
