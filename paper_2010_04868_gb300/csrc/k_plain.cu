@@ -58,7 +58,7 @@ __host__ __device__ constexpr int plain_rb()
 }
 
 template <int DIM, int SHAPE, int R, int ARITH>
-__global__ void __launch_bounds__(256) k_jacobi_plain(const double* __restrict__ u, double* __restrict__ v, Geo g,
+__global__ void __launch_bounds__(256, DIM == 3 ? 3 : 1) k_jacobi_plain(const double* __restrict__ u, double* __restrict__ v, Geo g,
                                                       int bc, double c, WArr<Stn<DIM, SHAPE, R>::K> w)
 {
     constexpr int RB = plain_rb<DIM, Stn<DIM, SHAPE, R>::K>();

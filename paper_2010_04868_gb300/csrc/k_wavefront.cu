@@ -11,7 +11,8 @@
 //
 // On GB300 the vector is a warp (vl = 32 sweeps):
 //
-// 1D. Lane k of the warp for sweep block b updates x = n - s*k at step n.
+// 1D. Lane k of the warp for sweep block b updates x = n - s*k at step n
+//     (s = r + 2, see k_gs1d_wave).
 //     After each step it passes its output one lane up with __shfl_up_sync;
 //     that value is exactly the newest previous-sweep value lane k+1 needs
 //     next (the rotate + blend of Algorithm 3). Lane 0 loads its
@@ -50,7 +51,7 @@
 namespace gbst {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int SPIN_LIMIT = 1 << 22;  // x ~0.5 us sleep: a wait gives up after about two seconds
+constexpr int SPIN_LIMIT = 1 << 23;  // x ~0.25-0.5 us per poll: a wait gives up after two to four seconds
 
 // Bounded-wait settings of one launch: poll limit, and a tile/block whose
 // completion is never published (-1: none; used only by failure-detection tests).
@@ -99,12 +100,17 @@ __device__ __noinline__ int64_t wait_progress(const unsigned long long* p, int64
     return INT64_MAX;
 }
 
+// Lane k holds sweep t0 + k at x = step - S*k with S = R + 2, one more than
+// legality needs: the previous-sweep value a lane receives from lane k-1 at a
+// step is already the newest one it needs at the NEXT step, so the partial sum
+// over the previous-sweep terms (+R .. 0) is formed one step ahead, and only
+// the R newest-value terms (-1 .. -R) remain on the step-to-step chain.
 template <int R, int ARITH>
 __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_t n, double c, WArr<2 * R + 1> w,
                                                   int64_t T, unsigned long long* progress, int* ticket, int* status,
                                                   unsigned tag, WaitCfg wc)
 {
-    constexpr int S = R + 1;
+    constexpr int S = R + 2;
     const int lane = threadIdx.x;
     int b = 0;
     if (lane == 0) b = atomicAdd(ticket, 1);
@@ -135,22 +141,29 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
     need_upto(n < 64 ? n : 64);
     double cur = load_chunk(0), nxt = load_chunk(1);
 
-    // old[o]: previous-sweep value at x - 1 + o (before the step's receive);
+    // ring[o]: previous-sweep value at x + o (o = 0..R) at the start of a step;
     // nw[a]: this sweep's value at x - 1 - a
-    double old[R + 1], nw[R];
+    double ring[R + 1], nw[R];
 #pragma unroll
     for (int o = 0; o <= R; ++o) {
-        const int64_t p = -1 + o;  // < 32: inside chunk 0
-        const double v = __shfl_sync(FULL, cur, (int)(p >= 0 ? p : 0));
-        old[o] = (lane == 0 && p >= 0 && p < n) ? v : c;
+        const double v = __shfl_sync(FULL, cur, o);
+        ring[o] = (lane == 0 && o < n) ? v : c;
     }
 #pragma unroll
     for (int a = 0; a < R; ++a) nw[a] = c;
+    // descending canonical order: +R .. +1, 0 (previous sweep), then -1 .. -R (this sweep)
+    auto partial = [&]() -> double {
+        double acc = __dmul_rn(w.w[0], ring[R]);
+#pragma unroll
+        for (int q = 1; q <= R; ++q) acc = acc_step<ARITH>(acc, w.w[q], ring[R - q]);
+        return acc;
+    };
+    double pc = partial();
     double out = c;
     const int64_t steps = n + (int64_t)S * (L - 1);
     for (int64_t step = 0; step < steps; ++step) {
         const int64_t x = step - (int64_t)S * lane;
-        const int64_t p = step + R;  // lane 0's newest previous-sweep position
+        const int64_t p = step + R + 1;  // newest previous-sweep position lane 0 takes in this step
         if ((p >> 5) != cur_ch) {
             cur_ch = p >> 5;
             cur = nxt;
@@ -161,13 +174,7 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
         const double bottom = __shfl_sync(FULL, cur, (int)(p & 31));
         double recv = __shfl_up_sync(FULL, out, 1);
         if (lane == 0) recv = p < n ? bottom : c;
-#pragma unroll
-        for (int o = 0; o < R; ++o) old[o] = old[o + 1];
-        old[R] = recv;
-        // descending canonical order: +R .. +1, 0 (previous sweep), -1 .. -R (this sweep)
-        double acc = __dmul_rn(w.w[0], old[R]);
-#pragma unroll
-        for (int q = 1; q <= R; ++q) acc = acc_step<ARITH>(acc, w.w[q], old[R - q]);
+        double acc = pc;
 #pragma unroll
         for (int a = 1; a <= R; ++a) acc = acc_step<ARITH>(acc, w.w[R + a], nw[a - 1]);
         const bool inside = x >= 0 && x < n;
@@ -175,6 +182,10 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
 #pragma unroll
         for (int a = R - 1; a > 0; --a) nw[a] = nw[a - 1];
         nw[0] = out;
+#pragma unroll
+        for (int o = 0; o < R; ++o) ring[o] = ring[o + 1];
+        ring[R] = recv;
+        pc = partial();
         if (top) {
             if (inside) u[x] = acc;
             if (publish && (step & 63) == 63 && x >= 0) {
@@ -250,9 +261,10 @@ __device__ void decode_tile(int64_t tk, const int64_t* __restrict__ pre, const W
 
 __device__ __forceinline__ bool wait_flag(const int* f, int tag, int spin)
 {
+    // poll tightly at first (a predecessor is usually about to finish), then back off
     for (int it = 0; it < spin; ++it) {
         if (ld_acquire(f) == tag) return true;
-        __nanosleep(500);
+        __nanosleep(it < 64 ? 32 : 256);
     }
     return false;
 }

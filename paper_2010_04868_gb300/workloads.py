@@ -1,0 +1,124 @@
+"""The benchmark workloads, runnable one at a time with a chosen kernel family.
+
+    python -m paper_2010_04868_gb300.workloads --config NAME [--kernel auto|plain|blocked|wavefront]
+                                               [--T STEPS] [--reps N] [--tb TB] [--tile A,B,C]
+
+Prints one JSON line per configuration: GStencil/s (point updates per second),
+the FP64-operation rate against the FP64 pipe's measured peak, and the
+algorithmic HBM bandwidth of one-pass-per-step execution. Inputs are the
+seeded synthetic grids of the recipes below (uniform [0, 1) values, seeded
+positive weights normalised to sum 1); they stand in for the synthetic
+benchmarks of the paper's Table 1.
+
+Configurations (name: stencil, grid, T, boundary):
+  heat1d      Jacobi 1D 3-point, weights (1/4, 1/2, 1/4), N = 65536, T = 256, zero halo
+  jacobi2d5   Jacobi 2D 5-point star, 4096^2, T = 1000, zero halo
+  jacobi2d9   Jacobi 2D 9-point box, 4096^2, T = 1000, zero halo
+  gs2d5       Gauss-Seidel 2D 5-point, 4096^2, T = 200, zero halo
+  gs1d3       Gauss-Seidel 1D 3-point, N = 2^24, T = 200, zero halo
+  jacobi3d7   Jacobi 3D 7-point star, 512^3, T = 100, periodic
+  jacobi3d27  Jacobi 3D 27-point box, 512^3, T = 100, periodic
+  gs3d7       Gauss-Seidel 3D 7-point, 512^3, T = 100, periodic
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+from . import inputs
+
+# FP64 pipe of this GPU: 1.684 lane operations (DFMA, DMUL or DADD) per SM clock, 152 SMs
+FP64_OPS_PER_SM_CLK = 1.684
+N_SM = 152
+
+CONFIGS = {
+    # name: (dim, shape, method, ext, T, bc, weights seed offset or explicit weights)
+    "heat1d": (1, 0, 0, (65536,), 256, 0, [0.25, 0.5, 0.25]),
+    "jacobi2d5": (2, 0, 0, (4096, 4096), 1000, 0, 105),
+    "jacobi2d9": (2, 1, 0, (4096, 4096), 1000, 0, 109),
+    "gs2d5": (2, 0, 1, (4096, 4096), 200, 0, 105),
+    "gs1d3": (1, 0, 1, (1 << 24,), 200, 0, 103),
+    "jacobi3d7": (3, 0, 0, (512, 512, 512), 100, 1, 207),
+    "jacobi3d27": (3, 1, 0, (512, 512, 512), 100, 1, 227),
+    "gs3d7": (3, 0, 1, (512, 512, 512), 100, 1, 208),
+}
+
+KERNELS = {"auto": 0, "plain": 1, "blocked": 2, "wavefront": 3}
+
+
+def k_points(dim, shape):
+    return 2 * dim + 1 if (shape == 0 or dim == 1) else 3 ** dim
+
+
+def config_weights(name):
+    dim, shape, _, _, _, _, w = CONFIGS[name]
+    if isinstance(w, list):
+        return list(w)
+    return list(inputs.normalized_weights(inputs.SEED_BASE + w, k_points(dim, shape)))
+
+
+def config_grid(name):
+    ext = CONFIGS[name][3]
+    return inputs.grid(inputs.SEED_BASE + 10 + list(CONFIGS).index(name), ext)
+
+
+def run(name, kernel="auto", T=None, reps=2, tb=0, tile=(0, 0, 0), sm_mhz=2070.0):
+    import torch
+
+    from . import stencil as S
+    dim, shape, method, ext, T0, bc, _ = CONFIGS[name]
+    T = T0 if T is None else T
+    u0 = torch.from_numpy(config_grid(name)).cuda()
+    st = S.Stencil(dim, shape, 1, config_weights(name), method, bc)
+    if kernel != "auto":
+        st.set_plan(KERNELS[kernel], tb, tile)
+    u = u0.clone()
+    scratch = torch.empty_like(u) if method == 0 else None
+    st.run(u, T, scratch)                       # warm-up (and tuning for the automatic plan)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        u.copy_(u0)
+        n0 = S.stencil_launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st.run(u, T, scratch)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if best is None or ms < best[0]:
+            best = (ms, S.stencil_launch_count() - n0)
+    rc = st.status()
+    st.close()
+    if rc != 0:
+        raise RuntimeError("%s: %s" % (name, S.strerror(rc)))
+    npts = 1
+    for e in ext:
+        npts *= e
+    ms, launches = best
+    gst = npts * T / ms / 1e6
+    k = k_points(dim, shape)
+    peak = FP64_OPS_PER_SM_CLK * N_SM * sm_mhz / 1e3
+    return {"config": name, "kernel": kernel, "T": T, "ms": round(ms, 3), "gstencil_s": round(gst, 3),
+            "launches": launches, "fp64_gops": round(gst * k, 1), "fp64_frac_of_peak": round(gst * k / peak, 4),
+            "hbm_gbs_one_pass_per_step": round(gst * 16, 1)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", default="all")
+    ap.add_argument("--kernel", default="auto", choices=list(KERNELS))
+    ap.add_argument("--T", type=int, default=None)
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--tb", type=int, default=0)
+    ap.add_argument("--tile", default="0,0,0")
+    a = ap.parse_args()
+    names = list(CONFIGS) if a.config == "all" else a.config.split(",")
+    tile = tuple(int(x) for x in a.tile.split(","))
+    for n in names:
+        print(json.dumps(run(n, a.kernel, a.T, a.reps, a.tb, tile)), flush=True)
+
+
+if __name__ == "__main__":
+    main()
