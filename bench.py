@@ -32,10 +32,15 @@ sys.path.insert(0, ROOT)
 N_SIDE = 4096
 T_STEPS = 1000
 STENCILS = (("2d5p", 0, 5), ("2d9p", 1, 9))   # name, shape id, K
-# FP64 pipe throughput measured on this GPU with a DFMA/DADD/DMUL micro-benchmark:
-# 1.684 lane-operations per SM clock (all three instructions alike), 152 SMs.
+# FP64 pipe throughput measured on this GPU with a DFMA/DADD/DMUL micro-benchmark
+# (python -m paper_2010_04868_gb300.peak): 1.684 lane operations per SM clock for
+# all three instructions, 152 SMs, i.e. 529.9 Gop/s at the 2070 MHz maximum clock.
 FP64_OPS_PER_SM_CLK = 1.684
 N_SM = 152
+# DRAM bytes (read + write) per launch of the plain 2D 9-point kernel on this
+# workload, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
+# the algorithmic figure is 16 B per point update, 268.4 MB per launch.
+NCU_TRAFFIC = {"Jacobi 2D 9P plain": 134_247_168 + 94_438_912}
 
 
 def _args():
@@ -219,6 +224,22 @@ def run_ours(args):
     per_stencil = {name: round(N_SIDE * N_SIDE * T_STEPS * args.steps / (times[name] * 1e-3) / 1e9, 3)
                    for name, _, _ in STENCILS}
 
+    # the plain per-step kernel on the same grids, one run of each stencil, for comparison
+    plain = {}
+    for name, _, _ in STENCILS:
+        wk = work[name]
+        wk["st"].set_plan(S.STENCIL_KERNEL_PLAIN)
+        wk["u"].copy_(u0)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        wk["st"].run(wk["u"], T_STEPS, wk["scratch"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain[name] = round(N_SIDE * N_SIDE * T_STEPS / (e0.elapsed_time(e1) * 1e-3) / 1e9, 3)
+        wk["st"].set_plan(S.STENCIL_KERNEL_AUTO)
+
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(work, u0_host, stream, S)
@@ -237,7 +258,7 @@ def run_ours(args):
                                    "T=1000 each, autotuned kernel", "grids": "2 x 4096^2", "T": T_STEPS,
                        "l2": "inputs (2 x 128 MiB grid + scratch) exceed L2; 512 MiB flush between steps",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "per_stencil_gstencil_s": per_stencil,
+            "per_stencil_gstencil_s": per_stencil, "plain_kernel_gstencil_s": plain,
             "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches),
             "e2e": e2e, "cpu_baseline": cpu,
         }
