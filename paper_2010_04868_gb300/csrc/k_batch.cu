@@ -1,25 +1,33 @@
 // Batched execution: many independent stencil problems in one persistent launch.
 //
 // Each problem is cut into phases of independent units:
-//   Jacobi, plain plan    one phase per time step; a unit is a chunk of points
+//   Jacobi, plain plan    one phase per time step; a unit is a slab of rows
+//                         (the plain kernel's thread mapping: several points per
+//                         thread along the slow axis)
 //   Jacobi, blocked plan  one phase per pass of T_b steps; a unit is one
 //                         staged tile (tile + T_b*r halo in shared memory,
 //                         T_b steps on chip, interior written once)
 //   Gauss-Seidel          one phase per (sweep, tile diagonal) of the
 //                         parallelogram tiling of the plain sweep kernel; a
 //                         unit is one tile (1D: the whole serial sweep)
-// A phase may start when every unit of the problem's previous phase has
-// finished (a per-problem completion counter). The work list interleaves the
-// problems round by round (phase 0 of every problem, then phase 1, ...), so a
-// unit only ever waits for units with smaller tickets; one persistent kernel
-// walks the list through a ticket counter and every wait is bounded. The
-// tiles and depths T_b come from each problem's tuned plan. Gauss-Seidel
-// problems whose plan is the wavefront kernel, and stencils with more than
-// 125 points, run as their own launches on the same stream. The whole
-// enqueue is captured once into a CUDA graph, cached on the batch's shape
-// (handles, pointers, extents, step counts, plans) and replayed afterwards.
-// Every point is computed with the same descending-order sum and rounding as
-// the single-problem kernels, so the results equal separate runs bit for bit.
+// A unit of a phase may run once every unit of the problem's previous phase
+// has finished (per-problem completion counter). CTAs claim units
+// dynamically: each problem hands out its units in order through its own
+// ticket counter, and a CTA takes the first unit of the first problem (in
+// order of decreasing phase count, so long dependence chains go first) whose
+// next phase is open. A unit claimed ahead of its phase waits (bounded) for
+// it; the units it waits for were all claimed earlier by running CTAs, so the
+// wait always ends. Jacobi and Gauss-Seidel-tile units of the common radius-1
+// stencils run the same compile-time specialised code as the single-problem
+// kernels; other stencils use run-time offset tables. The tiles and depths
+// T_b come from each problem's tuned plan. Gauss-Seidel problems whose plan
+// is the wavefront kernel, and stencils with more than 125 points, run as
+// their own launches on the same stream. The whole enqueue is captured once
+// into a CUDA graph, cached on the batch's shape (handles, pointers, extents,
+// step counts, plans) and replayed afterwards. Every point is computed with
+// the same descending-order sum and rounding as the single-problem kernels,
+// so the results equal separate runs bit for bit.
+#include <algorithm>
 #include <cstring>
 #include <list>
 #include <map>
@@ -36,20 +44,26 @@ namespace {
 
 constexpr int BT = 256;          // threads per batch CTA
 constexpr int BMAXK = 125;       // largest stencil the batch kernel takes
-constexpr int JCHUNK = 2048;     // points per plain Jacobi unit
-constexpr int BSPIN = 1 << 23;   // bounded waits (x ~0.25 us)
+constexpr int J1CHUNK = 8192;    // points per 1D Jacobi unit
+constexpr int J2ROWS = 4;        // rows per 2D Jacobi unit (one row per unrolled point)
+constexpr int J3PLANES = 2;      // planes per 3D Jacobi unit ...
+constexpr int J3ROWS = 8;        // ... times rows
+constexpr int BSPIN = 1 << 23;   // bounded waits (x ~0.1-0.25 us)
 
 enum { BK_JPLAIN = 0, BK_JBLOCK = 1, BK_GSTILE = 2, BK_GS1D = 3 };
+// compile-time specialisations: (dim, shape, r = 1)
+enum { SP_NONE = 0, SP_1S = 1, SP_2S = 2, SP_2B = 3, SP_3S = 4, SP_3B = 5 };
 
 struct BProb {
-    int kind, dim, K, r, bc, arith;
+    int kind, spec, dim, K, r, bc, arith;
     double c;
     const double* w;  // descending canonical order
     const int* off;   // 3 per term, same order
     double* a;        // the grid (result)
     double* b;        // scratch (Jacobi)
     Geo g;
-    int64_t T, nph, units;
+    int64_t T, nph, units, total;
+    int64_t nj8;      // 3D Jacobi units per plane pair
     // blocked Jacobi
     int B0, B1, B2, h0, h1, h2, E0, E1, E2, tb;
     int64_t nt0, nt1, nt2;
@@ -57,7 +71,8 @@ struct BProb {
     int gb0, gb1, gbs, cp0, cp1, skew;
     int64_t gnt0, gnt1, gnts, Dn, sweep_units;
     const int64_t* dpre;           // units on diagonals before D (Dn + 1 entries)
-    unsigned long long* done;      // completed units
+    unsigned long long* next;      // units handed out
+    unsigned long long* done;      // units completed
     int* status;
 };
 
@@ -68,13 +83,28 @@ __device__ __forceinline__ unsigned long long ld_acq64(const unsigned long long*
     return v;
 }
 
-__device__ __forceinline__ int64_t units_of(const BProb& P, int64_t ph)
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// phase of unit ticket t, and its index within the phase
+__device__ __forceinline__ int64_t phase_of(const BProb& P, int64_t t, int64_t& unit)
 {
     if (P.kind == BK_GSTILE) {
-        const int64_t D = ph % P.Dn;
-        return P.dpre[D + 1] - P.dpre[D];
+        const int64_t sw = t / P.sweep_units, rem = t % P.sweep_units;
+        int64_t lo = 0, hi = P.Dn - 1;  // last D with dpre[D] <= rem
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (P.dpre[mid] <= rem) lo = mid; else hi = mid - 1;
+        }
+        unit = rem - P.dpre[lo];
+        return sw * P.Dn + lo;
     }
-    return P.units;
+    unit = t % P.units;
+    return t / P.units;
 }
 
 __device__ __forceinline__ int64_t units_before(const BProb& P, int64_t ph)
@@ -83,14 +113,7 @@ __device__ __forceinline__ int64_t units_before(const BProb& P, int64_t ph)
     return ph * P.units;
 }
 
-// weighted sum with run-time offsets: values v[] already fetched
-template <int ARITH>
-__device__ __forceinline__ double chain(const double* w, const double* v, int K)
-{
-    double acc = __dmul_rn(w[0], v[0]);
-    for (int q = 1; q < K; ++q) acc = acc_step<ARITH>(acc, w[q], v[q]);
-    return acc;
-}
+// ---- run-time-offset paths (any stencil up to BMAXK points)
 
 template <int ARITH>
 __device__ double point_bc(const double* u, int64_t i, int64_t j, int64_t k, const BProb& P, const double* sw,
@@ -138,23 +161,83 @@ __device__ __forceinline__ bool interior(const BProb& P, int64_t i, int64_t j, i
            (k >= r && k < P.g.n2 - r);
 }
 
-template <int ARITH>
-__device__ void unit_jplain(const BProb& P, int64_t ph, int64_t unit, const double* sw, const int* so, long long* lo)
+// Points of plain Jacobi unit u, visited as (i, j, k) with the same mapping for
+// the specialised and the run-time paths: f(i, j, k, linear index).
+template <bool UNROLL3 = true, typename F>
+__device__ __forceinline__ void for_jacobi_unit(const BProb& P, int64_t u, F f)
 {
-    const double* src = (ph & 1) ? P.b : P.a;
-    double* dst = (ph & 1) ? P.a : P.b;
-    const int64_t n12 = P.g.n1 * P.g.n2, npts = P.g.n0 * n12;
-    for (int q = threadIdx.x; q < P.K; q += BT) lo[q] = (long long)so[3 * q] * n12 + so[3 * q + 1] * P.g.n2 + so[3 * q + 2];
-    __syncthreads();
-    const int64_t beg = unit * JCHUNK, end = beg + JCHUNK < npts ? beg + JCHUNK : npts;
-    for (int64_t p = beg + threadIdx.x; p < end; p += BT) {
-        const int64_t i = p / n12, j = (p / P.g.n2) % P.g.n1, k = p % P.g.n2;
-        dst[p] = interior(P, i, j, k) ? point_lin<ARITH>(src, p, lo, sw, P.K) : point_bc<ARITH>(src, i, j, k, P, sw, so);
+    const Geo& g = P.g;
+    const int tid = threadIdx.x;
+    if (P.dim == 1) {
+        const int64_t beg = u * J1CHUNK;
+#pragma unroll 4
+        for (int m = 0; m < J1CHUNK / BT; ++m) {
+            const int64_t k = beg + m * BT + tid;
+            if (k < g.n2) f(0, 0, k, k);
+        }
+    } else if (P.dim == 2) {
+        const int64_t j0 = u * J2ROWS;
+        for (int64_t k = tid; k < g.n2; k += BT)
+#pragma unroll
+            for (int rb = 0; rb < J2ROWS; ++rb) {
+                const int64_t j = j0 + rb;
+                if (j < g.n1) f(0, j, k, j * g.n2 + k);
+            }
+    } else {
+        const int64_t i0 = (u / P.nj8) * J3PLANES, j0 = (u % P.nj8) * J3ROWS;
+        const int tx = tid % 64, ty = tid / 64;
+        for (int jj = ty; jj < J3ROWS; jj += BT / 64) {
+            const int64_t j = j0 + jj;
+            if (j >= g.n1) break;
+            for (int64_t k = tx; k < g.n2; k += 64) {
+                if (UNROLL3) {
+#pragma unroll
+                    for (int rb = 0; rb < J3PLANES; ++rb) {
+                        const int64_t i = i0 + rb;
+                        if (i < g.n0) f(i, j, k, (i * g.n1 + j) * g.n2 + k);
+                    }
+                } else {
+#pragma unroll 1
+                    for (int rb = 0; rb < J3PLANES; ++rb) {
+                        const int64_t i = i0 + rb;
+                        if (i < g.n0) f(i, j, k, (i * g.n1 + j) * g.n2 + k);
+                    }
+                }
+            }
+        }
     }
 }
 
+template <int DIM, int SHAPE, int ARITH>
+__device__ __noinline__ void unit_jplain_sp(const BProb& P, int64_t ph, int64_t u, const double* sw)
+{
+    const double* src = (ph & 1) ? P.b : P.a;
+    double* dst = (ph & 1) ? P.a : P.b;
+    const int64_t s1 = P.g.n2, s0 = P.g.n1 * P.g.n2;
+    // a 3D box keeps one point in flight per thread: two would not fit the register budget
+    for_jacobi_unit<!(DIM == 3 && SHAPE == BOX)>(P, u, [&](int64_t i, int64_t j, int64_t k, int64_t p) {
+        const bool in = (DIM < 3 || (i >= 1 && i < P.g.n0 - 1)) && (DIM < 2 || (j >= 1 && j < P.g.n1 - 1)) &&
+                        k >= 1 && k < P.g.n2 - 1;
+        dst[p] = in ? update_interior<DIM, SHAPE, 1, ARITH, false>(src, p, s0, s1, sw)
+                    : update_bc<DIM, SHAPE, 1, ARITH>(src, i, j, k, P.g, P.bc, P.c, sw);
+    });
+}
+
 template <int ARITH>
-__device__ void unit_jblock(const BProb& P, int64_t ph, int64_t unit, const double* sw, const int* so, long long* lo,
+__device__ __noinline__ void unit_jplain_rt(const BProb& P, int64_t ph, int64_t u, const double* sw, const int* so, long long* lo)
+{
+    const double* src = (ph & 1) ? P.b : P.a;
+    double* dst = (ph & 1) ? P.a : P.b;
+    const int64_t n12 = P.g.n1 * P.g.n2;
+    for (int q = threadIdx.x; q < P.K; q += BT) lo[q] = (long long)so[3 * q] * n12 + so[3 * q + 1] * P.g.n2 + so[3 * q + 2];
+    __syncthreads();
+    for_jacobi_unit(P, u, [&](int64_t i, int64_t j, int64_t k, int64_t p) {
+        dst[p] = interior(P, i, j, k) ? point_lin<ARITH>(src, p, lo, sw, P.K) : point_bc<ARITH>(src, i, j, k, P, sw, so);
+    });
+}
+
+template <int ARITH>
+__device__ __noinline__ void unit_jblock(const BProb& P, int64_t ph, int64_t unit, const double* sw, const int* so, long long* lo,
                             double* sm)
 {
     const double* src = (ph & 1) ? P.b : P.a;
@@ -169,8 +252,7 @@ __device__ void unit_jblock(const BProb& P, int64_t ph, int64_t unit, const doub
     for (int q = threadIdx.x; q < P.K; q += BT) lo[q] = (long long)so[3 * q] * st0 + so[3 * q + 1] * st1 + so[3 * q + 2];
     for (int64_t idx = threadIdx.x; idx < region; idx += BT) {
         const int64_t i = g0 + idx / st0, j = g1 + (idx / st1) % P.E1, k = g2 + idx % st1;
-        const double v = fetch_bc(src, i, j, k, P.g, P.bc, P.c);
-        A[idx] = v;
+        A[idx] = fetch_bc(src, i, j, k, P.g, P.bc, P.c);
         if (P.bc == BC_CONSTANT && (i < 0 || i >= P.g.n0 || j < 0 || j >= P.g.n1 || k < 0 || k >= P.g.n2)) B[idx] = P.c;
     }
     __syncthreads();
@@ -205,12 +287,13 @@ __device__ void unit_jblock(const BProb& P, int64_t ph, int64_t unit, const doub
     }
 }
 
-template <int ARITH>
-__device__ void unit_gstile(const BProb& P, int64_t ph, int64_t unit, const double* sw, const int* so)
+// tile (T0, T1, TS) of the problem's parallelogram tiling for diagonal D
+__device__ __forceinline__ void gs_tile_of(const BProb& P, int64_t D, int64_t unit, int64_t& T0, int64_t& T1,
+                                           int64_t& TS)
 {
-    const int64_t D = ph % P.Dn;
-    // unit -> (T0, T1) among the tiles with 0 <= D - T0 - T1 < gnts
-    int64_t T0 = 0, T1 = 0, rem = unit;
+    T0 = 0;
+    T1 = 0;
+    int64_t rem = unit;
     for (int64_t t0 = 0; t0 < P.gnt0; ++t0) {
         int64_t lo = D - t0 - P.gnts + 1, hi = D - t0;
         if (lo < 0) lo = 0;
@@ -223,101 +306,147 @@ __device__ void unit_gstile(const BProb& P, int64_t ph, int64_t unit, const doub
         }
         rem -= cnt;
     }
-    const int64_t TS = D - T0 - T1;
+    TS = D - T0 - T1;
+}
+
+template <int DIM, int SHAPE, int ARITH, bool SPEC>
+__device__ __noinline__ void unit_gstile(const BProb& P, int64_t ph, int64_t unit, const double* sw, const int* so)
+{
+    int64_t T0, T1, TS;
+    gs_tile_of(P, ph % P.Dn, unit, T0, T1, TS);
     double* u = P.a;
     const int l1 = threadIdx.x % P.gb1, l0 = threadIdx.x / P.gb1;
     const int64_t i = T0 * P.gb0 + l0;
     const int64_t j = T1 * P.gb1 + l1 - (int64_t)P.skew * i;
     const bool owner = l0 < P.gb0 && i < P.g.n0 && j >= 0 && j < P.g.n1;
     const int64_t kb = TS * P.gbs - (int64_t)P.cp0 * i - (int64_t)P.cp1 * j;
+    const int64_t s1 = P.g.n2, s0 = P.g.n1 * P.g.n2;
+    const bool in01 = (DIM < 3 || (i >= 1 && i < P.g.n0 - 1)) && (j >= 1 && j < P.g.n1 - 1);
     for (int ls = 0; ls < P.gbs; ++ls) {
         const int64_t k = kb + ls;
-        if (owner && k >= 0 && k < P.g.n2) u[(i * P.g.n1 + j) * P.g.n2 + k] = point_bc<ARITH>(u, i, j, k, P, sw, so);
+        if (owner && k >= 0 && k < P.g.n2) {
+            const int64_t p = i * s0 + j * s1 + k;
+            double r;
+            if (SPEC)
+                r = (in01 && k >= 1 && k < P.g.n2 - 1) ? update_interior<DIM, SHAPE, 1, ARITH, false>(u, p, s0, s1, sw)
+                                                       : update_bc<DIM, SHAPE, 1, ARITH>(u, i, j, k, P.g, P.bc, P.c, sw);
+            else
+                r = point_bc<ARITH>(u, i, j, k, P, sw, so);
+            u[p] = r;
+        }
         __syncthreads();
     }
 }
 
 template <int ARITH>
-__device__ void unit_gs1d(const BProb& P, const double* sw, const int* so)
+__device__ __noinline__ void unit_gs1d(const BProb& P, const double* sw, const int* so)
 {
     if (threadIdx.x != 0) return;
     for (int64_t k = 0; k < P.g.n2; ++k) P.a[k] = point_bc<ARITH>(P.a, 0, 0, k, P, sw, so);
 }
 
-__global__ void __launch_bounds__(BT) k_batch(const BProb* __restrict__ probs, int np, const int64_t* __restrict__ rpre,
-                                             int64_t nrounds, unsigned long long* ticket)
+template <int ARITH>
+__device__ void run_unit(const BProb& P, int64_t ph, int64_t u, const double* sw, const int* so, long long* lo,
+                         double* dyn)
+{
+    switch (P.kind) {
+        case BK_JPLAIN:
+            switch (P.spec) {
+                case SP_1S: unit_jplain_sp<1, STAR, ARITH>(P, ph, u, sw); break;
+                case SP_2S: unit_jplain_sp<2, STAR, ARITH>(P, ph, u, sw); break;
+                case SP_2B: unit_jplain_sp<2, BOX, ARITH>(P, ph, u, sw); break;
+                case SP_3S: unit_jplain_sp<3, STAR, ARITH>(P, ph, u, sw); break;
+                case SP_3B: unit_jplain_sp<3, BOX, ARITH>(P, ph, u, sw); break;
+                default: unit_jplain_rt<ARITH>(P, ph, u, sw, so, lo);
+            }
+            break;
+        case BK_JBLOCK: unit_jblock<ARITH>(P, ph, u, sw, so, lo, dyn); break;
+        case BK_GSTILE:
+            switch (P.spec) {
+                case SP_2S: unit_gstile<2, STAR, ARITH, true>(P, ph, u, sw, so); break;
+                case SP_2B: unit_gstile<2, BOX, ARITH, true>(P, ph, u, sw, so); break;
+                case SP_3S: unit_gstile<3, STAR, ARITH, true>(P, ph, u, sw, so); break;
+                case SP_3B: unit_gstile<3, BOX, ARITH, true>(P, ph, u, sw, so); break;
+                default: unit_gstile<3, STAR, ARITH, false>(P, ph, u, sw, so);
+            }
+            break;
+        default: unit_gs1d<ARITH>(P, sw, so);
+    }
+}
+
+__global__ void __launch_bounds__(BT, 2) k_batch(const BProb* __restrict__ probs, int np, const int* __restrict__ order)
 {
     extern __shared__ __align__(16) double bsm[];
-    __shared__ long long s_tk;
+    __shared__ __align__(16) BProb sP;
     __shared__ int s_p;
     __shared__ long long s_ph, s_unit;
     __shared__ double s_w[BMAXK];
     __shared__ int s_off[3 * BMAXK];
     __shared__ long long s_lo[BMAXK];
-    const int64_t total = rpre[nrounds];
     for (;;) {
         if (threadIdx.x == 0) {
-            s_tk = (long long)atomicAdd(ticket, 1ull);
-            if (s_tk < total) {
-                int64_t lo = 0, hi = nrounds - 1;
-                while (lo < hi) {
-                    const int64_t mid = (lo + hi + 1) / 2;
-                    if (rpre[mid] <= s_tk) lo = mid; else hi = mid - 1;
+            // claim: the first problem (longest dependence chain first) whose next unit's phase is open
+            int p = -1;
+            long long tk = 0;
+            for (int spin = 0; spin < BSPIN && p < 0; ++spin) {
+                bool all_out = true;
+                for (int oi = 0; oi < np && p < 0; ++oi) {
+                    const BProb& Q = probs[order[oi]];
+                    const unsigned long long nx = ld_relaxed64(Q.next);
+                    if (nx >= (unsigned long long)Q.total) continue;
+                    all_out = false;
+                    int64_t uu;
+                    const int64_t ph = phase_of(Q, (int64_t)nx, uu);
+                    if (ld_relaxed64(Q.done) < (unsigned long long)units_before(Q, ph)) continue;
+                    const unsigned long long t = atomicAdd(Q.next, 1ull);
+                    if (t >= (unsigned long long)Q.total) continue;
+                    p = order[oi];
+                    tk = (long long)t;
                 }
-                int64_t rem = s_tk - rpre[lo];
-                int p = 0;
-                for (; p < np; ++p) {
-                    if (lo >= probs[p].nph) continue;
-                    const int64_t u = units_of(probs[p], lo);
-                    if (rem < u) break;
-                    rem -= u;
-                }
-                s_p = p;
-                s_ph = lo;
-                s_unit = rem;
-                // wait until the problem's previous phase has finished
-                const BProb& P = probs[p];
-                const unsigned long long need = (unsigned long long)units_before(P, lo);
+                if (all_out) break;
+                if (p < 0) __nanosleep(spin < 64 ? 32 : 128);
+            }
+            s_p = p;
+            if (p >= 0) {
+                const BProb& Q = probs[p];
+                int64_t uu;
+                const int64_t ph = phase_of(Q, tk, uu);
+                s_ph = ph;
+                s_unit = uu;
+                // a unit claimed ahead of its phase waits for the units claimed before it
+                const unsigned long long need = (unsigned long long)units_before(Q, ph);
                 int it = 0;
-                while (ld_acq64(P.done) < need && it < BSPIN) {
-                    __nanosleep(256);
+                while (ld_acq64(Q.done) < need && it < BSPIN) {
+                    __nanosleep(it < 64 ? 32 : 128);
                     ++it;
                 }
-                if (it >= BSPIN) atomicExch(P.status, DEV_TIMEOUT);
+                if (it >= BSPIN) atomicExch(Q.status, DEV_TIMEOUT);
+                __threadfence();
             }
         }
         __syncthreads();
-        if (s_tk >= total) return;
-        const BProb& P = probs[s_p];
-        for (int q = threadIdx.x; q < P.K; q += BT) {
-            s_w[q] = P.w[q];
-            s_off[3 * q] = P.off[3 * q];
-            s_off[3 * q + 1] = P.off[3 * q + 1];
-            s_off[3 * q + 2] = P.off[3 * q + 2];
+        if (s_p < 0) return;
+        {
+            const int* src = (const int*)&probs[s_p];
+            int* dst = (int*)&sP;
+            for (int q = threadIdx.x; q < (int)(sizeof(BProb) / sizeof(int)); q += BT) dst[q] = src[q];
         }
         __syncthreads();
-        const bool fma = P.arith == ARITH_FMA;
-        switch (P.kind) {
-            case BK_JPLAIN:
-                if (fma) unit_jplain<ARITH_FMA>(P, s_ph, s_unit, s_w, s_off, s_lo);
-                else unit_jplain<ARITH_UNFUSED>(P, s_ph, s_unit, s_w, s_off, s_lo);
-                break;
-            case BK_JBLOCK:
-                if (fma) unit_jblock<ARITH_FMA>(P, s_ph, s_unit, s_w, s_off, s_lo, bsm);
-                else unit_jblock<ARITH_UNFUSED>(P, s_ph, s_unit, s_w, s_off, s_lo, bsm);
-                break;
-            case BK_GSTILE:
-                if (fma) unit_gstile<ARITH_FMA>(P, s_ph, s_unit, s_w, s_off);
-                else unit_gstile<ARITH_UNFUSED>(P, s_ph, s_unit, s_w, s_off);
-                break;
-            default:
-                if (fma) unit_gs1d<ARITH_FMA>(P, s_w, s_off);
-                else unit_gs1d<ARITH_UNFUSED>(P, s_w, s_off);
+        for (int q = threadIdx.x; q < sP.K; q += BT) {
+            s_w[q] = sP.w[q];
+            s_off[3 * q] = sP.off[3 * q];
+            s_off[3 * q + 1] = sP.off[3 * q + 1];
+            s_off[3 * q + 2] = sP.off[3 * q + 2];
         }
+        __syncthreads();
+        if (sP.arith == ARITH_FMA)
+            run_unit<ARITH_FMA>(sP, s_ph, s_unit, s_w, s_off, s_lo, bsm);
+        else
+            run_unit<ARITH_UNFUSED>(sP, s_ph, s_unit, s_w, s_off, s_lo, bsm);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(P.done, 1ull);
+            atomicAdd(sP.done, 1ull);
         }
     }
 }
@@ -327,10 +456,10 @@ __global__ void __launch_bounds__(BT) k_batch(const BProb* __restrict__ probs, i
 // Everything a batch of a given shape needs on the device, prepared once.
 struct BatchEntry {
     cudaGraphExec_t exec = nullptr;  // the captured enqueue (absent until first launched outside a capture)
-    char* dev = nullptr;             // descriptors, tables, counters, ticket
-    size_t off_probs = 0, off_rpre = 0, off_done = 0, total_bytes = 0, off_ticket = 0;
+    char* dev = nullptr;             // descriptors, claim order, GS tables, counters
+    size_t off_probs = 0, off_order = 0, off_cnt = 0, total_bytes = 0;
     int np = 0;
-    int64_t maxph = 0, nblk = 1;
+    int64_t nblk = 1;
     size_t smem = 0;
     std::vector<double*> copy_dst, copy_src;  // Jacobi results that end in scratch
     std::vector<size_t> copy_bytes;
@@ -355,14 +484,6 @@ int64_t count_gs_units(const BProb& P, int64_t D)
     }
     return n;
 }
-
-struct Built {
-    std::vector<BProb> probs;
-    std::vector<std::vector<int64_t>> dpre;  // per problem (GS tiles)
-    std::vector<int64_t> rpre;
-    size_t smem = 0;
-    int64_t nrounds = 0;
-};
 
 // Fill the descriptor of problem i (device pointers patched in later).
 bool describe(stencil_handle_s* h, const stencil_grid* g, int64_t T, const Plan& pl, BProb& P)
@@ -406,15 +527,22 @@ bool describe(stencil_handle_s* h, const stencil_grid* g, int64_t T, const Plan&
         }
         if (P.kind != BK_JBLOCK) {
             P.kind = BK_JPLAIN;
-            P.units = (npts + JCHUNK - 1) / JCHUNK;
+            if (h->dim == 1) P.units = (npts + J1CHUNK - 1) / J1CHUNK;
+            if (h->dim == 2) P.units = (P.g.n1 + J2ROWS - 1) / J2ROWS;
+            if (h->dim == 3) {
+                P.nj8 = (P.g.n1 + J3ROWS - 1) / J3ROWS;
+                P.units = (P.g.n0 + J3PLANES - 1) / J3PLANES * P.nj8;
+            }
             P.nph = T;
         }
+        P.total = P.units * P.nph;
         return true;
     }
     if (h->dim == 1) {
         P.kind = BK_GS1D;
         P.units = 1;
         P.nph = T;
+        P.total = T;
         return true;
     }
     if (h->bc == BC_PERIODIC && h->shape == BOX) return false;
@@ -432,7 +560,16 @@ bool describe(stencil_handle_s* h, const stencil_grid* g, int64_t T, const Plan&
     P.gnts = thmax / P.gbs + 1;
     P.Dn = (P.gnt0 - 1) + (P.gnt1 - 1) + (P.gnts - 1) + 1;
     P.nph = T * P.Dn;
-    return true;
+    return true;  // total is set once the tile counts per diagonal are known
+}
+
+// compile-time specialisation available for (dim, shape, r)
+int spec_of(const stencil_handle_s* h)
+{
+    if (h->r != 1) return SP_NONE;
+    if (h->dim == 1) return SP_1S;
+    if (h->dim == 2) return h->shape == STAR ? SP_2S : SP_2B;
+    return h->shape == STAR ? SP_3S : SP_3B;
 }
 
 }  // namespace
@@ -460,6 +597,8 @@ int batch_run(const stencil_handle* hs, const stencil_grid* gs, const int64_t* T
         const bool wave = h->method == GAUSS_SEIDEL && plans[i].kernel == STENCIL_KERNEL_WAVEFRONT &&
                           gs_wavefront_supported(h, make_geo(h->dim, gs[i].ext));
         if (!wave && h->K <= BMAXK && describe(h, &gs[i], Ts[i], plans[i], P)) {
+            P.spec = spec_of(h);
+            if (P.kind == BK_GSTILE && h->dim == 1) P.spec = SP_NONE;
             inside.push_back(i);
             probs.push_back(P);
         } else {
@@ -484,10 +623,9 @@ int batch_run(const stencil_handle* hs, const stencil_grid* gs, const int64_t* T
 
     auto enqueue = [&](const BatchEntry& e, cudaStream_t s) -> int {
         if (e.np > 0) {
-            if (cudaMemsetAsync(e.dev + e.off_done, 0, e.total_bytes - e.off_done, s) != cudaSuccess) return STENCIL_ECUDA;
+            if (cudaMemsetAsync(e.dev + e.off_cnt, 0, e.total_bytes - e.off_cnt, s) != cudaSuccess) return STENCIL_ECUDA;
             k_batch<<<(unsigned)e.nblk, BT, e.smem, s>>>((const BProb*)(e.dev + e.off_probs), e.np,
-                                                          (const int64_t*)(e.dev + e.off_rpre), e.maxph,
-                                                          (unsigned long long*)(e.dev + e.off_ticket));
+                                                          (const int*)(e.dev + e.off_order));
             if (cudaGetLastError() != cudaSuccess) return STENCIL_ECUDA;
             for (size_t q = 0; q < e.copy_dst.size(); ++q)
                 if (cudaMemcpyAsync(e.copy_dst[q], e.copy_src[q], e.copy_bytes[q], cudaMemcpyDeviceToDevice, s) !=
@@ -539,50 +677,43 @@ int batch_run(const stencil_handle* hs, const stencil_grid* gs, const int64_t* T
     const int np = (int)probs.size();
     e.np = np;
     std::vector<std::vector<int64_t>> dpre(np);
-    int64_t maxph = 0;
     size_t smem = 0;
+    int64_t total_units = 0;
     for (int p = 0; p < np; ++p) {
         BProb& P = probs[p];
         if (P.kind == BK_GSTILE) {
             dpre[p].assign((size_t)P.Dn + 1, 0);
             for (int64_t D = 0; D < P.Dn; ++D) dpre[p][(size_t)D + 1] = dpre[p][(size_t)D] + count_gs_units(P, D);
             P.sweep_units = dpre[p][(size_t)P.Dn];
+            P.total = P.sweep_units * P.T;
         }
         if (P.kind == BK_JBLOCK) {
             const int64_t region = (int64_t)P.E0 * P.E1 * P.E2;
             const size_t b = (size_t)(((region + 31) & ~int64_t(31)) + region) * 8;
             if (b > smem) smem = b;
         }
-        if (P.nph > maxph) maxph = P.nph;
+        total_units += P.total;
         if ((P.kind == BK_JPLAIN || P.kind == BK_JBLOCK) && (P.nph & 1)) {
             e.copy_dst.push_back(P.a);
             e.copy_src.push_back(P.b);
             e.copy_bytes.push_back((size_t)(P.g.n0 * P.g.n1 * P.g.n2) * sizeof(double));
         }
     }
-    std::vector<int64_t> rpre((size_t)maxph + 1, 0);
-    for (int64_t r = 0; r < maxph; ++r) {
-        int64_t tot = 0;
-        for (int p = 0; p < np; ++p) {
-            const BProb& P = probs[p];
-            if (r >= P.nph) continue;
-            tot += P.kind == BK_GSTILE ? dpre[p][(size_t)(r % P.Dn) + 1] - dpre[p][(size_t)(r % P.Dn)] : P.units;
-        }
-        rpre[(size_t)r + 1] = rpre[(size_t)r] + tot;
-    }
+    // claim order: longest dependence chain (most phases) first
+    std::vector<int> order(np);
+    for (int p = 0; p < np; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return probs[x].nph > probs[y].nph; });
     e.off_probs = 0;
-    e.off_rpre = ((size_t)np * sizeof(BProb) + 255) & ~size_t(255);
-    const size_t off_dpre = e.off_rpre + ((rpre.size() * 8 + 255) & ~size_t(255));
+    e.off_order = ((size_t)np * sizeof(BProb) + 255) & ~size_t(255);
+    const size_t off_dpre = e.off_order + (((size_t)np * sizeof(int) + 255) & ~size_t(255));
     std::vector<size_t> dpre_off(np, 0);
     size_t cur = off_dpre;
     for (int p = 0; p < np; ++p) {
         dpre_off[p] = cur;
         cur += (dpre[p].size() * 8 + 255) & ~size_t(255);
     }
-    e.off_done = cur;
-    e.off_ticket = e.off_done + (((size_t)np * 8 + 255) & ~size_t(255));
-    e.total_bytes = e.off_ticket + 256;
-    e.maxph = maxph;
+    e.off_cnt = cur;  // per problem: units handed out, units completed
+    e.total_bytes = e.off_cnt + (((size_t)np * 16 + 255) & ~size_t(255));
     e.smem = smem;
     if (np > 0) {
         if (cudaMalloc(&e.dev, e.total_bytes) != cudaSuccess) {
@@ -591,11 +722,13 @@ int batch_run(const stencil_handle* hs, const stencil_grid* gs, const int64_t* T
         }
         for (int p = 0; p < np; ++p) {
             probs[p].dpre = probs[p].kind == BK_GSTILE ? (const int64_t*)(e.dev + dpre_off[p]) : nullptr;
-            probs[p].done = (unsigned long long*)(e.dev + e.off_done) + p;
+            probs[p].next = (unsigned long long*)(e.dev + e.off_cnt) + 2 * p;
+            probs[p].done = (unsigned long long*)(e.dev + e.off_cnt) + 2 * p + 1;
         }
         bool ok = cudaMemcpy(e.dev + e.off_probs, probs.data(), (size_t)np * sizeof(BProb), cudaMemcpyHostToDevice) ==
                       cudaSuccess &&
-                  cudaMemcpy(e.dev + e.off_rpre, rpre.data(), rpre.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+                  cudaMemcpy(e.dev + e.off_order, order.data(), (size_t)np * sizeof(int), cudaMemcpyHostToDevice) ==
+                      cudaSuccess;
         for (int p = 0; p < np && ok; ++p)
             if (!dpre[p].empty())
                 ok = cudaMemcpy(e.dev + dpre_off[p], dpre[p].data(), dpre[p].size() * 8, cudaMemcpyHostToDevice) ==
@@ -611,7 +744,6 @@ int batch_run(const stencil_handle* hs, const stencil_grid* gs, const int64_t* T
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BT, smem);
         if (per_sm < 1) per_sm = 1;
         e.nblk = (int64_t)nsm * per_sm;
-        const int64_t total_units = rpre[(size_t)maxph];
         if (e.nblk > total_units) e.nblk = total_units > 0 ? total_units : 1;
     }
 
