@@ -200,6 +200,136 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
     }
 }
 
+// Radius 1, three warps per sweep block. One warp issues at most one FP64
+// instruction per ~64 clocks, so the single-warp kernel spends three of those
+// per step. Here the three terms of a lane's update are issued by three warps
+// (on three SM sub-partitions), a pipeline through shared memory with one CTA
+// barrier per step:
+//   warp 0  term +1 (the first product) of point m = s + 2
+//   warp 1  term  0 (first fused add)   of point m = s + 1
+//   warp 2  term -1 (newest value)      of point m = s, and the output
+// At loop step s every warp reads only values written before the previous
+// barrier: its predecessor's partial sum (double-buffered by point parity) and
+// lane k-1's outputs from a ring of the last 8 steps. Lane k holds sweep t0+k
+// at x = m - 4k; the skew 4 = 2r + 2 makes the previous-sweep value warp 0
+// needs for point m (lane k-1's output at x + 1) appear at step m - 3, one
+// step before warp 0 handles m. Lane 0 of warps 0 and 1 takes the grid's
+// values (the previous sweep block's output) from 32-value chunks as above.
+__device__ __forceinline__ void bar_sync96() { asm volatile("bar.sync 1, 96;" ::: "memory"); }
+
+template <int ARITH>
+__global__ void __launch_bounds__(96) k_gs1d_wave3(double* __restrict__ u, int64_t n, double c, WArr<3> w, int64_t T,
+                                                   unsigned long long* progress, int* ticket, int* status,
+                                                   unsigned tag, WaitCfg wc)
+{
+    constexpr int S = 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ int s_b;
+    __shared__ double acc0[2][32], acc1[2][32], outr[8][32];
+    if (threadIdx.x == 0) s_b = atomicAdd(ticket, 1);
+    for (int q = threadIdx.x; q < 8 * 32; q += 96) (&outr[0][0])[q] = c;
+    for (int q = threadIdx.x; q < 2 * 32; q += 96) {
+        (&acc0[0][0])[q] = 0.0;
+        (&acc1[0][0])[q] = 0.0;
+    }
+    __syncthreads();
+    const int b = s_b;
+    const int64_t nB = (T + 31) / 32;
+    if (b >= nB) return;
+    const int L = (int)((T - 32 * (int64_t)b) < 32 ? (T - 32 * (int64_t)b) : 32);
+    const unsigned long long* prev = b > 0 ? progress + b - 1 : nullptr;
+    unsigned long long* mine = progress + b;
+    const bool publish = b != wc.stall;
+    const unsigned long long mytag = (unsigned long long)tag << PROG_SHIFT;
+    int64_t known = b > 0 ? 0 : INT64_MAX;
+    auto need_upto = [&](int64_t upto) {
+        if (lane == 0 && upto > known) known = wait_progress(prev, upto, tag, status, wc.spin);
+        __syncwarp();
+    };
+    auto load_chunk = [&](int64_t ch) -> double {
+        const int64_t p = ch * 32 + lane;
+        return (p >= 0 && p < n) ? __ldcg(u + p) : c;
+    };
+    const int64_t steps = n + (int64_t)S * (L - 1);
+    // The step loop runs in chunks of 32 steps starting at s0 = -32 (the first
+    // two steps that matter are s = -2, -1: pipeline fill). With s0 a multiple
+    // of 32, every ring slot, buffer parity and shuffle lane below is a
+    // compile-time constant of the unrolled step j, and each warp's grid
+    // position crosses into its next 32-value chunk at a fixed j.
+    if (warp < 2) {
+        // warp 0: term +1 of point s + 2, grid position s + 3; warp 1: term 0 of point s + 1, position s + 1
+        const int OFF = warp == 0 ? 3 : 1;
+        double cur = c;                // chunk (s0 + OFF) >> 5 at the start of a chunk of steps
+        need_upto(n < 32 ? n : 32);
+        double nxt = load_chunk(0);
+        for (int64_t s0 = -32; s0 < steps; s0 += 32) {
+            const int64_t c0 = s0 >> 5;
+            const bool first = s0 < 0;  // outputs of steps < 0 do not exist: previous-sweep values are c
+            if (warp == 0) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    if (j == 29) {     // position s0 + j + 3 enters chunk c0 + 1
+                        cur = nxt;
+                        const int64_t upto = (c0 + 3) * 32;
+                        need_upto(upto < n ? upto : n);
+                        nxt = load_chunk(c0 + 2);
+                    }
+                    const double bottom = __shfl_sync(FULL, cur, (j + 3) & 31);
+                    double v = (first || lane == 0) ? c : outr[(j + 7) & 7][lane - 1];
+                    if (lane == 0 && s0 + j + 3 < n) v = bottom;
+                    acc0[j & 1][lane] = __dmul_rn(w.w[0], v);
+                    bar_sync96();
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    if (j == 31) {     // position s0 + j + 1 enters chunk c0 + 1
+                        cur = nxt;
+                        const int64_t upto = (c0 + 3) * 32;
+                        need_upto(upto < n ? upto : n);
+                        nxt = load_chunk(c0 + 2);
+                    }
+                    const double bottom = __shfl_sync(FULL, cur, (j + 1) & 31);
+                    double v = (first || lane == 0) ? c : outr[(j + 5) & 7][lane - 1];
+                    if (lane == 0 && s0 + j + 1 >= 0 && s0 + j + 1 < n) v = bottom;
+                    acc1[(j + 1) & 1][lane] = acc_step<ARITH>(acc0[(j + 1) & 1][lane], w.w[1], v);
+                    bar_sync96();
+                }
+            }
+            (void)OFF;
+        }
+    } else {
+        double nw = c;  // this lane's previous output
+        const bool top = lane == L - 1;
+        for (int64_t s0 = -32; s0 < steps; s0 += 32) {
+            if (s0 < 0) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) bar_sync96();
+                continue;
+            }
+            const int64_t x0 = s0 - (int64_t)S * lane;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int64_t x = x0 + j;
+                const double acc = acc_step<ARITH>(acc1[j & 1][lane], w.w[2], nw);
+                const bool inside = x >= 0 && x < n;
+                nw = inside ? acc : c;
+                outr[j & 7][lane] = nw;
+                if (top && inside) u[x] = acc;
+                bar_sync96();
+            }
+            if (top && publish && ((s0 >> 5) & 1) && x0 + 31 >= 0) {
+                __threadfence();
+                st_release64(mine, mytag | (unsigned long long)(x0 + 32 < n ? x0 + 32 : n));
+            }
+        }
+        if (top && publish) {
+            __threadfence();
+            st_release64(mine, mytag | (unsigned long long)n);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ 2D/3D ---
 
 struct WaveGeo {
@@ -467,12 +597,22 @@ static int wave_1d(const RunCtx& ctx, double* u, int64_t T, bool prepare_only = 
     const unsigned tag = 1;
     if (cudaMemsetAsync(h->wave_ws, 0, bytes, ctx.st) != cudaSuccess) return STENCIL_ECUDA;
     const WaitCfg wc = take_wait_cfg(h);
-    if (h->arith == ARITH_FMA)
+    if (R == 1) {
+        WArr<3> w3;
+        for (int q = 0; q < 3; ++q) w3.w[q] = w.w[q];
+        if (h->arith == ARITH_FMA)
+            k_gs1d_wave3<ARITH_FMA><<<(unsigned)nB, 96, 0, ctx.st>>>(u, ctx.g.n2, h->c, w3, T, progress, ticket,
+                                                                      h->d_status, tag, wc);
+        else
+            k_gs1d_wave3<ARITH_UNFUSED><<<(unsigned)nB, 96, 0, ctx.st>>>(u, ctx.g.n2, h->c, w3, T, progress, ticket,
+                                                                          h->d_status, tag, wc);
+    } else if (h->arith == ARITH_FMA) {
         k_gs1d_wave<R, ARITH_FMA><<<(unsigned)nB, 32, 0, ctx.st>>>(u, ctx.g.n2, h->c, w, T, progress, ticket,
                                                                      h->d_status, tag, wc);
-    else
+    } else {
         k_gs1d_wave<R, ARITH_UNFUSED><<<(unsigned)nB, 32, 0, ctx.st>>>(u, ctx.g.n2, h->c, w, T, progress, ticket,
                                                                          h->d_status, tag, wc);
+    }
     g_launches++;
     return cuda_rc(cudaGetLastError());
 }
