@@ -61,6 +61,21 @@ def _dist():
     return world, rank, local
 
 
+def aggregate(total_ms, world, dist=None, device=None):
+    """Max over ranks of the timed milliseconds (every rank must call it when world > 1)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return float(total_ms)
+
+
+def job_value(updates_per_rank_step, world, ms_per_step):
+    """Whole-job throughput in GStencil/s: every rank processes its own replica in ms_per_step."""
+    return world * updates_per_rank_step / (ms_per_step * 1e-3) / 1e9
+
+
 def weights(k):
     from paper_2010_04868_gb300 import inputs
     return inputs.normalized_weights(inputs.SEED_BASE + 100 + k, k)
@@ -196,14 +211,10 @@ def run_ours(args):
         if rc != 0:
             raise RuntimeError("device status after timing: " + S.strerror(rc))
 
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-
+    total_ms = aggregate(total_ms, world, dist, dev)
     updates_per_step = len(STENCILS) * N_SIDE * N_SIDE * T_STEPS
     ms_per_step = total_ms / args.steps
-    value = world * updates_per_step / (ms_per_step * 1e-3) / 1e9
+    value = job_value(updates_per_step, world, ms_per_step)
 
     # dominant kernel: the stencil with the larger share of the time
     dom = max(times, key=times.get)
