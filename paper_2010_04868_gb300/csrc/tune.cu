@@ -108,7 +108,17 @@ std::vector<Plan> jacobi_candidates(const stencil_handle_s* h, const Geo& g, int
         if (tb <= T) c.push_back(Plan{STENCIL_KERNEL_BLOCKED, tb, {t0, t1, t2}});
     };
     if (h->dim == 1) {
-        for (int64_t tile : {256, 432, 1024})
+        // tiles that spread the grid evenly over 1-4 CTAs per SM (one even wave), and two fixed sizes
+        int nsm = 152, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        std::vector<int64_t> tiles = {256, 1024};
+        for (int m = 1; m <= 4; ++m) {
+            int64_t t = (g.n2 + (int64_t)nsm * m - 1) / ((int64_t)nsm * m);
+            t = (t + 1) & ~int64_t(1);
+            if (t >= 64 && t <= 4096) tiles.push_back(t);
+        }
+        for (int64_t tile : tiles)
             for (int tb : {16, 32, 64}) add(tb / h->r > 0 ? tb / h->r : 1, 0, 0, tile);
     } else if (h->dim == 2) {
         for (int tb : {2, 3, 4}) {
