@@ -594,7 +594,10 @@ int batch_run(const stencil_handle* hs, const stencil_grid* gs, const int64_t* T
         if (Ts[i] == 0) continue;
         stencil_handle_s* h = hs[i];
         BProb P;
-        const bool wave = h->method == GAUSS_SEIDEL && plans[i].kernel == STENCIL_KERNEL_WAVEFRONT &&
+        // the time-skewed wavefront (constant boundary) runs as its own launch; periodic Gauss-Seidel
+        // cannot overlap its sweeps anyway and stays in the shared kernel as tile units
+        const bool wave = h->method == GAUSS_SEIDEL && h->bc == BC_CONSTANT &&
+                          plans[i].kernel == STENCIL_KERNEL_WAVEFRONT &&
                           gs_wavefront_supported(h, make_geo(h->dim, gs[i].ext));
         if (!wave && h->K <= BMAXK && describe(h, &gs[i], Ts[i], plans[i], P)) {
             P.spec = spec_of(h);

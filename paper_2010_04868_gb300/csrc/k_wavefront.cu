@@ -399,6 +399,15 @@ __device__ __forceinline__ bool wait_flag(const int* f, int tag, int spin)
     return false;
 }
 
+__device__ __forceinline__ bool wait_flag_ge(const int* f, int tag, int spin)
+{
+    for (int it = 0; it < spin; ++it) {
+        if (ld_acquire(f) >= tag) return true;
+        __nanosleep(it < 64 ? 32 : 256);
+    }
+    return false;
+}
+
 // Which window cells a point update reads: every cell for a box; for a star
 // the centre row in full and the other rows only above/below the points.
 template <int SHAPE, int R, int W>
@@ -540,12 +549,139 @@ __global__ void k_wave_prefix(WaveGeo wg, int64_t* pre)
     }
 }
 
+// ---------------------------------------------------- periodic: in-sweep DAG ---
+//
+// With a periodic boundary, sweep t+1 reads (through the wrap) values sweep t
+// writes last, so sweeps cannot overlap (no time skew is legal). Inside a
+// sweep the parallelogram tiling of the plain kernel still applies: in
+// (i, sigma, theta) coordinates every newest-value dependence points to a
+// tile with all coordinates <= (and not all equal), every old-value read to
+// one with all coordinates >=. Instead of one launch per tile diagonal, one
+// persistent launch runs all T sweeps: tiles are handed out in (sweep,
+// diagonal) order, each waits (bounded) for its three lower neighbours of the
+// same sweep and for every tile of the previous sweep, computes its points in
+// theta order (one CTA barrier per theta), and publishes its flag.
+
+struct SweepDag {
+    int b0, b1, bs, cp0, cp1, skew;   // tile extents in (i, sigma, theta), hyperplane weights, sigma skew
+    int64_t nt0, nt1, nts, Dn, sweep_units, T;
+};
+
+__device__ __forceinline__ int64_t count_tiles_on(const SweepDag& t, int64_t D)
+{
+    int64_t n = 0;
+    for (int64_t t0 = 0; t0 < t.nt0; ++t0) {
+        int64_t lo = D - t0 - t.nts + 1, hi = D - t0;
+        if (lo < 0) lo = 0;
+        if (hi > t.nt1 - 1) hi = t.nt1 - 1;
+        if (hi >= lo) n += hi - lo + 1;
+    }
+    return n;
+}
+
+__global__ void k_sweepdag_prefix(SweepDag t, int64_t* pre)
+{
+    for (int64_t d = threadIdx.x; d < t.Dn; d += blockDim.x) pre[d + 1] = count_tiles_on(t, d);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        pre[0] = 0;
+        for (int64_t d = 0; d < t.Dn; ++d) pre[d + 1] += pre[d];
+    }
+}
+
+template <int DIM, int SHAPE, int R, int ARITH>
+__global__ void __launch_bounds__(256) k_gs_sweepdag(double* __restrict__ u, Geo g, int bc, double c,
+                                                     WArr<Stn<DIM, SHAPE, R>::K> w, SweepDag t,
+                                                     const int64_t* __restrict__ pre, int* __restrict__ flags,
+                                                     unsigned long long* __restrict__ ctr, int* status, WaitCfg wc)
+{
+    __shared__ long long s_T0, s_T1, s_TS, s_sw;
+    __shared__ int s_go;
+    unsigned long long* ticket = ctr;
+    unsigned long long* finished = ctr + 1;
+    const int64_t total = t.sweep_units * t.T;
+    const int64_t s1 = g.n2, s0 = g.n1 * g.n2;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long tk = (long long)atomicAdd(ticket, 1ull);
+            s_go = tk < total;
+            if (s_go) {
+                const int64_t sw = tk / t.sweep_units, rem = tk % t.sweep_units;
+                int64_t lo = 0, hi = t.Dn - 1;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi + 1) / 2;
+                    if (pre[mid] <= rem) lo = mid; else hi = mid - 1;
+                }
+                const int64_t D = lo;
+                int64_t r = rem - pre[D], T0 = 0, T1 = 0;
+                for (int64_t t0 = 0; t0 < t.nt0; ++t0) {
+                    int64_t a = D - t0 - t.nts + 1, b = D - t0;
+                    if (a < 0) a = 0;
+                    if (b > t.nt1 - 1) b = t.nt1 - 1;
+                    const int64_t cnt = b >= a ? b - a + 1 : 0;
+                    if (r < cnt) {
+                        T0 = t0;
+                        T1 = a + r;
+                        break;
+                    }
+                    r -= cnt;
+                }
+                const int64_t TS = D - T0 - T1;
+                s_T0 = T0;
+                s_T1 = T1;
+                s_TS = TS;
+                s_sw = sw;
+                // the whole previous sweep, then the three lower neighbours of this sweep
+                bool ok = true;
+                int it = 0;
+                while (ld_acquire64(finished) < (unsigned long long)(sw * t.sweep_units) && it < wc.spin) {
+                    __nanosleep(it < 64 ? 32 : 256);
+                    ++it;
+                }
+                ok &= it < wc.spin;
+                const int tag = (int)sw + 1;
+                const int64_t f = (T0 * t.nt1 + T1) * t.nts + TS;
+                if (T0 > 0) ok &= wait_flag_ge(flags + f - t.nt1 * t.nts, tag, wc.spin);
+                if (T1 > 0) ok &= wait_flag_ge(flags + f - t.nts, tag, wc.spin);
+                if (TS > 0) ok &= wait_flag_ge(flags + f - 1, tag, wc.spin);
+                if (!ok) atomicExch(status, DEV_TIMEOUT);
+                __threadfence();
+            }
+        }
+        __syncthreads();
+        if (!s_go) return;
+        const int l1 = threadIdx.x % t.b1, l0 = threadIdx.x / t.b1;
+        const int64_t i = s_T0 * t.b0 + l0;
+        const int64_t j = s_T1 * t.b1 + l1 - (int64_t)t.skew * i;
+        const bool owner = l0 < t.b0 && i < g.n0 && j >= 0 && j < g.n1;
+        const int64_t kb = s_TS * t.bs - (int64_t)t.cp0 * i - (int64_t)t.cp1 * j;
+        const bool in01 = (DIM < 3 || (i >= R && i < g.n0 - R)) && (j >= R && j < g.n1 - R);
+        for (int ls = 0; ls < t.bs; ++ls) {
+            const int64_t k = kb + ls;
+            if (owner && k >= 0 && k < g.n2) {
+                const int64_t p = i * s0 + j * s1 + k;
+                u[p] = (in01 && k >= R && k < g.n2 - R) ? update_interior<DIM, SHAPE, R, ARITH, false>(u, p, s0, s1, w.w)
+                                                        : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w.w);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const int64_t f = (s_T0 * t.nt1 + s_T1) * t.nts + s_TS;
+            __threadfence();
+            if (s_sw * t.sweep_units + f != wc.stall) st_release(flags + f, (int)s_sw + 1);
+            atomicAdd(finished, 1ull);
+        }
+    }
+}
+
 // ------------------------------------------------------------------- host ---
 
 bool gs_wavefront_supported(const stencil_handle_s* h, const Geo& g)
 {
     (void)g;
-    if (h->method != GAUSS_SEIDEL || h->bc != BC_CONSTANT) return false;
+    if (h->method != GAUSS_SEIDEL) return false;
+    if (h->bc == BC_PERIODIC)  // in-sweep tile DAG: stars in 2D/3D (a periodic box has no hyperplane order)
+        return h->dim >= 2 && h->shape == STAR && h->r <= 2;
     if (h->dim == 1) return h->r >= 1 && h->r <= 4;
     if (h->dim == 2) return h->r <= 2;
     return h->r == 1;
@@ -701,9 +837,69 @@ static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes, bool p
     return cuda_rc(cudaGetLastError());
 }
 
+template <int DIM, int SHAPE, int R>
+static int sweep_dag(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
+{
+    stencil_handle_s* h = ctx.h;
+    constexpr int K = Stn<DIM, SHAPE, R>::K;
+    WArr<K> w;
+    for (int q = 0; q < K; ++q) w.w[q] = h->w_desc[q];
+    const Geo& g = ctx.g;
+    const bool box = SHAPE == BOX;
+    SweepDag t;
+    t.cp1 = box ? 1 + R : 1;
+    t.cp0 = DIM == 3 ? (box ? 1 + R * (t.cp1 + 1) : 1) : 0;
+    t.skew = (DIM == 3 && box) ? R : 0;
+    // small tiles: a sweep's critical path is about nt0 + nt1 + nts tiles long
+    if (DIM == 3) {
+        t.b0 = 8; t.b1 = 8; t.bs = 16;
+    } else {
+        t.b0 = 1; t.b1 = 64; t.bs = 32;
+    }
+    const int64_t thmax = t.cp0 * (g.n0 - 1) + t.cp1 * (g.n1 - 1) + (g.n2 - 1);
+    t.nt0 = (g.n0 + t.b0 - 1) / t.b0;
+    t.nt1 = (g.n1 + t.skew * (g.n0 - 1) + t.b1 - 1) / t.b1;
+    t.nts = thmax / t.bs + 1;
+    t.Dn = (t.nt0 - 1) + (t.nt1 - 1) + (t.nts - 1) + 1;
+    t.sweep_units = t.nt0 * t.nt1 * t.nts;
+    t.T = T;
+    if (t.sweep_units > (int64_t)1 << 30) return STENCIL_EUNSUPPORTED;
+    const size_t pre_bytes = (size_t)(t.Dn + 1) * sizeof(int64_t);
+    const size_t flag_off = 256 + ((pre_bytes + 255) & ~size_t(255));
+    const size_t bytes = flag_off + (size_t)t.sweep_units * sizeof(int);
+    int rc = wave_workspace(h, bytes, ctx.st);
+    if (rc || prepare_only) return rc;
+    unsigned long long* ctr = (unsigned long long*)h->wave_ws;  // ticket, finished
+    int64_t* dpre = (int64_t*)((char*)h->wave_ws + 256);
+    int* flags = (int*)((char*)h->wave_ws + flag_off);
+    if (cudaMemsetAsync(ctr, 0, 16, ctx.st) != cudaSuccess) return STENCIL_ECUDA;
+    if (cudaMemsetAsync(flags, 0, (size_t)t.sweep_units * sizeof(int), ctx.st) != cudaSuccess) return STENCIL_ECUDA;
+    k_sweepdag_prefix<<<1, 256, 0, ctx.st>>>(t, dpre);
+    g_launches++;
+    auto kern = h->arith == ARITH_FMA ? k_gs_sweepdag<DIM, SHAPE, R, ARITH_FMA> : k_gs_sweepdag<DIM, SHAPE, R, ARITH_UNFUSED>;
+    int nsm = 0, per_sm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int nthr = t.b0 * t.b1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nthr, 0);
+    int64_t nblk = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
+    if (nblk > t.sweep_units * T) nblk = t.sweep_units * T;
+    const WaitCfg wc = take_wait_cfg(h);
+    kern<<<(unsigned)nblk, nthr, 0, ctx.st>>>(u, g, h->bc, h->c, w, t, dpre, flags, ctr, h->d_status, wc);
+    g_launches++;
+    return cuda_rc(cudaGetLastError());
+}
+
 static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, bool prep)
 {
     const stencil_handle_s* h = ctx.h;
+    if (h->bc == BC_PERIODIC) {  // sweeps cannot overlap: one persistent launch, tiles in a DAG per sweep
+        if (h->dim == 2 && h->shape == STAR && h->r == 1) return sweep_dag<2, STAR, 1>(ctx, u, T, prep);
+        if (h->dim == 2 && h->shape == STAR && h->r == 2) return sweep_dag<2, STAR, 2>(ctx, u, T, prep);
+        if (h->dim == 3 && h->shape == STAR && h->r == 1) return sweep_dag<3, STAR, 1>(ctx, u, T, prep);
+        if (h->dim == 3 && h->shape == STAR && h->r == 2) return sweep_dag<3, STAR, 2>(ctx, u, T, prep);
+        return STENCIL_EUNSUPPORTED;
+    }
     if (h->dim == 1) {
         switch (h->r) {
             case 1: return wave_1d<1>(ctx, u, T, prep);

@@ -73,13 +73,14 @@ def test_gs1d_long_wavefront_equals_oracle():
     assert bits_equal(got, ref), first_diff(got, ref)
 
 
-@pytest.mark.parametrize("dim,ext,unit", [(1, (5000,), 0), (2, (40, 50), 3), (3, (8, 9, 10), 5)])
-def test_stalled_producer_times_out_without_hanging(dim, ext, unit):
+@pytest.mark.parametrize("dim,ext,unit,bc", [(1, (5000,), 0, 0), (2, (40, 50), 3, 0), (3, (8, 9, 10), 5, 0),
+                                             (3, (20, 21, 22), 2, 1)])
+def test_stalled_producer_times_out_without_hanging(dim, ext, unit, bc):
     """A producer that never publishes makes its consumers' bounded waits expire: ETIMEOUT, no hang."""
     import torch
     from paper_2010_04868_gb300 import stencil as S
     w, u0 = case(dim, "star", 1, ext, seed=5)
-    st = S.Stencil(dim, 0, 1, list(w), S.STENCIL_GAUSS_SEIDEL).set_plan(WAVE)
+    st = S.Stencil(dim, 0, 1, list(w), S.STENCIL_GAUSS_SEIDEL, bc).set_plan(WAVE)
     u = torch.from_numpy(u0.copy()).cuda()
     S.stencil_debug_inject_stall(st.handle, unit, 20000)
     st.run(u, 70)
@@ -88,15 +89,40 @@ def test_stalled_producer_times_out_without_hanging(dim, ext, unit):
     u.copy_(torch.from_numpy(u0))
     st.run(u, 70)
     assert st.status() == 0
-    ref = oracle_run(u0, 70, dim, "star", 1, w, "gs", "constant", 0.0, "fma")
+    ref = oracle_run(u0, 70, dim, "star", 1, w, "gs", "periodic" if bc else "constant", 0.0, "fma")
     assert bits_equal(u.cpu().numpy(), ref)
     st.close()
 
 
-def test_periodic_wavefront_is_rejected():
+PERIODIC_CASES = [(2, 1, (37, 40)), (2, 1, (130, 300)), (2, 2, (21, 33)), (3, 1, (5, 6, 7)), (3, 1, (20, 33, 40)),
+                  (3, 2, (9, 10, 11))]
+
+
+@pytest.mark.parametrize("dim,r,ext", PERIODIC_CASES)
+def test_periodic_star_sweep_dag(dim, r, ext):
+    """Periodic stars: sweeps cannot overlap; the in-sweep tile DAG in one launch matches the oracle."""
+    w, u0 = case(dim, "star", r, ext, seed=dim * 10 + r + 90)
+    for T in (1, 3, 8):
+        for arith in ("fma", "unfused"):
+            ref = oracle_run(u0, T, dim, "star", r, w, "gs", "periodic", 0.0, arith)
+            got = gpu_run(u0, T, dim, "star", r, w, "gs", "periodic", 0.0, arith, plan=WAVE)
+            assert bits_equal(got, ref), (T, arith, first_diff(got, ref))
+
+
+def test_periodic_3d_full_size_sweep_dag_equals_plain():
+    """512^3 periodic Gauss-Seidel 7-point, 6 sweeps: the one-launch DAG equals the per-diagonal plain kernel."""
+    from paper_2010_04868_gb300 import inputs
+    u0 = inputs.grid(inputs.SEED_BASE + 7, (512, 512, 512))
+    w = inputs.normalized_weights(inputs.SEED_BASE + 208, 7)
+    a = gpu_run(u0, 6, 3, "star", 1, w, "gs", "periodic", 0.0, "fma", plan=WAVE)
+    b = gpu_run(u0, 6, 3, "star", 1, w, "gs", "periodic", 0.0, "fma", plan=PLAIN)
+    assert bits_equal(a, b), first_diff(a, b)
+
+
+def test_periodic_box_wavefront_is_rejected():
     import torch
     from paper_2010_04868_gb300 import stencil as S
-    st = S.Stencil(2, 0, 1, [0.2] * 5, S.STENCIL_GAUSS_SEIDEL, S.STENCIL_BC_PERIODIC).set_plan(WAVE)
+    st = S.Stencil(2, 1, 1, [0.1] * 9, S.STENCIL_GAUSS_SEIDEL, S.STENCIL_BC_PERIODIC).set_plan(WAVE)
     with pytest.raises(S.StencilError) as e:
         st.run(torch.zeros(8, 8, dtype=torch.float64, device="cuda"), 3)
     assert e.value.code == S.STENCIL_EUNSUPPORTED
