@@ -6,7 +6,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/stencil.h"
+#include "stencil.h"  // include/ (the build passes -I include)
 #include "common.cuh"
 
 struct stencil_handle_s {

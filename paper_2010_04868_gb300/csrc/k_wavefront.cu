@@ -828,7 +828,9 @@ static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes, bool p
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
-    int64_t nblk = (int64_t)nsm * (per_sm > 4 ? 4 : (per_sm > 0 ? per_sm : 1));
+    // two CTAs (8 worker warps) per SM: more tiles in flight would slow the tiles on the DAG's
+    // critical path (they share the FP64 pipe); fewer leave it idle
+    int64_t nblk = (int64_t)nsm * (per_sm > 2 ? 2 : (per_sm > 0 ? per_sm : 1));
     const int64_t need = (wg.ntiles + 3) / 4;
     if (nblk > need) nblk = need;
     const WaitCfg wc = take_wait_cfg(h);

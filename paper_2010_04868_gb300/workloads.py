@@ -19,6 +19,10 @@ Configurations (name: stencil, grid, T, boundary):
   jacobi3d7   Jacobi 3D 7-point star, 512^3, T = 100, periodic
   jacobi3d27  Jacobi 3D 27-point box, 512^3, T = 100, periodic
   gs3d7       Gauss-Seidel 3D 7-point, 512^3, T = 100, periodic
+  jacobi1d5   Jacobi 1D 5-point (radius 2), N = 2^24, T = 100, zero halo
+  jacobi2d9s  Jacobi 2D 9-point star (radius 2), 4096^2, T = 200, zero halo
+  jacobi3d13  Jacobi 3D 13-point star (radius 2), 256^3, T = 100, zero halo
+  gs2d9s      Gauss-Seidel 2D 9-point star (radius 2), 4096^2, T = 100, zero halo
   batch3d     jacobi3d7 + jacobi3d27 + gs3d7 in one stencil_run_batch call (one persistent launch
               replayed from a CUDA graph), against the same three run one after another
 """
@@ -43,20 +47,27 @@ CONFIGS = {
     "jacobi3d7": (3, 0, 0, (512, 512, 512), 100, 1, 207),
     "jacobi3d27": (3, 1, 0, (512, 512, 512), 100, 1, 227),
     "gs3d7": (3, 0, 1, (512, 512, 512), 100, 1, 208),
+    # higher order (radius 2)
+    "jacobi1d5": (1, 0, 0, (1 << 24,), 100, 0, 305),
+    "jacobi2d9s": (2, 0, 0, (4096, 4096), 200, 0, 309),
+    "jacobi3d13": (3, 0, 0, (256, 256, 256), 100, 0, 313),
+    "gs2d9s": (2, 0, 1, (4096, 4096), 100, 0, 319),
 }
+
+RADIUS = {"jacobi1d5": 2, "jacobi2d9s": 2, "jacobi3d13": 2, "gs2d9s": 2}
 
 KERNELS = {"auto": 0, "plain": 1, "blocked": 2, "wavefront": 3}
 
 
-def k_points(dim, shape):
-    return 2 * dim + 1 if (shape == 0 or dim == 1) else 3 ** dim
+def k_points(dim, shape, r=1):
+    return 2 * dim * r + 1 if (shape == 0 or dim == 1) else (2 * r + 1) ** dim
 
 
 def config_weights(name):
     dim, shape, _, _, _, _, w = CONFIGS[name]
     if isinstance(w, list):
         return list(w)
-    return list(inputs.normalized_weights(inputs.SEED_BASE + w, k_points(dim, shape)))
+    return list(inputs.normalized_weights(inputs.SEED_BASE + w, k_points(dim, shape, RADIUS.get(name, 1))))
 
 
 def config_grid(name):
@@ -69,9 +80,10 @@ def run(name, kernel="auto", T=None, reps=2, tb=0, tile=(0, 0, 0), sm_mhz=2070.0
 
     from . import stencil as S
     dim, shape, method, ext, T0, bc, _ = CONFIGS[name]
+    r = RADIUS.get(name, 1)
     T = T0 if T is None else T
     u0 = torch.from_numpy(config_grid(name)).cuda()
-    st = S.Stencil(dim, shape, 1, config_weights(name), method, bc)
+    st = S.Stencil(dim, shape, r, config_weights(name), method, bc)
     if kernel != "auto":
         st.set_plan(KERNELS[kernel], tb, tile)
     u = u0.clone()
@@ -100,9 +112,9 @@ def run(name, kernel="auto", T=None, reps=2, tb=0, tile=(0, 0, 0), sm_mhz=2070.0
         npts *= e
     ms, launches = best
     gst = npts * T / ms / 1e6
-    k = k_points(dim, shape)
+    k = k_points(dim, shape, r)
     peak = FP64_OPS_PER_SM_CLK * N_SM * sm_mhz / 1e3
-    return {"config": name, "kernel": kernel, "T": T, "ms": round(ms, 3), "gstencil_s": round(gst, 3),
+    return {"config": name, "kernel": kernel, "r": r, "T": T, "ms": round(ms, 3), "gstencil_s": round(gst, 3),
             "launches": launches, "fp64_gops": round(gst * k, 1), "fp64_frac_of_peak": round(gst * k / peak, 4),
             "hbm_gbs_one_pass_per_step": round(gst * 16, 1)}
 
