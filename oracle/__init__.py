@@ -50,6 +50,12 @@ def load(path: str):
                                ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
                                ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     lib.oracle_run.restype = ctypes.c_int
+    if hasattr(lib, "oracle_run_field"):
+        lib.oracle_run_field.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        lib.oracle_run_field.restype = ctypes.c_int
     lib.oracle_max_threads.restype = ctypes.c_int
     return lib
 
@@ -80,17 +86,28 @@ def max_threads() -> int:
 
 def run(u, T: int, *, dim: int, shape: int, r: int, weights, method: int = JACOBI,
         bc: int = BC_CONSTANT, c: float = 0.0, arith: int = ARITH_FMA, nthreads: int = 0,
-        lib=None) -> np.ndarray:
-    """Return the grid after T steps (u is not modified). lib: an alternative library from load()."""
+        lib=None, field=None) -> np.ndarray:
+    """Return the grid after T steps (u is not modified). lib: an alternative library from load().
+
+    field: optional per-point weights of shape (K,) + grid shape in canonical term order; it
+    replaces the constant weights (which still give K).
+    """
     lib = lib if lib is not None else _load()
     a = np.array(u, dtype=np.float64, order="C", copy=True)
     if a.ndim != dim:
         raise ValueError("grid rank %d != dim %d" % (a.ndim, dim))
     w = np.ascontiguousarray(weights, dtype=np.float64)
     ext = (ctypes.c_int64 * 3)(*(list(a.shape) + [1] * (3 - dim)))
-    rc = lib.oracle_run(dim, shape, r, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(w),
-                        method, bc, float(c), arith, ext, int(T),
-                        a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(nthreads))
+    dptr = ctypes.POINTER(ctypes.c_double)
+    if field is None:
+        rc = lib.oracle_run(dim, shape, r, w.ctypes.data_as(dptr), len(w), method, bc, float(c), arith, ext, int(T),
+                            a.ctypes.data_as(dptr), int(nthreads))
+    else:
+        f = np.ascontiguousarray(field, dtype=np.float64)
+        if f.shape != (len(w),) + a.shape:
+            raise ValueError("field must have shape (K,) + grid shape")
+        rc = lib.oracle_run_field(dim, shape, r, w.ctypes.data_as(dptr), f.ctypes.data_as(dptr), len(w), method, bc,
+                                  float(c), arith, ext, int(T), a.ctypes.data_as(dptr), int(nthreads))
     if rc != 0:
         raise ValueError("oracle_run rejected its arguments")
     return a

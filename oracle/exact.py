@@ -36,12 +36,14 @@ def _rnd(x: Fraction) -> Fraction:
 
 
 def run(u, T, *, dim, shape, r, weights, method="jacobi", bc="constant", c=0.0, rounding=None,
-        require_representable=False):
+        require_representable=False, field=None):
     """u: nested lists or numpy array; returns a dict {index tuple: Fraction}.
 
     require_representable: with rounding=None, raise ArithmeticError if any
     product or partial sum is not exactly a float64 (the case is then unfit
     for a bit-exact comparison with a float implementation).
+    field: optional per-point weights, array of shape (K,) + grid shape in
+    canonical term order; the weight of term q at point p is field[q][p].
     """
     import numpy as np
 
@@ -50,6 +52,10 @@ def run(u, T, *, dim, shape, r, weights, method="jacobi", bc="constant", c=0.0, 
     offs = canonical_offsets(dim, shape, r)
     assert len(offs) == len(weights)
     W = [Fraction(float(w)) for w in weights]
+    F = None if field is None else np.asarray(field, dtype=np.float64)
+
+    def wt(q, p):
+        return W[q] if F is None else Fraction(float(F[(q,) + tuple(p)]))
     C = Fraction(float(c))
     pts = list(itertools.product(*[range(n) for n in ext]))   # lexicographic order
     cur = {p: Fraction(float(arr[p])) for p in pts}
@@ -65,7 +71,7 @@ def run(u, T, *, dim, shape, r, weights, method="jacobi", bc="constant", c=0.0, 
     def point(state, p):
         order = list(range(len(offs) - 1, -1, -1))      # descending canonical order
         q0 = order[0]
-        acc = W[q0] * get(state, tuple(pi + oi for pi, oi in zip(p, offs[q0])))
+        acc = wt(q0, p) * get(state, tuple(pi + oi for pi, oi in zip(p, offs[q0])))
         if rounding is not None:
             acc = _rnd(acc)
         elif require_representable and _rnd(acc) != acc:
@@ -73,14 +79,14 @@ def run(u, T, *, dim, shape, r, weights, method="jacobi", bc="constant", c=0.0, 
         for q in order[1:]:
             v = get(state, tuple(pi + oi for pi, oi in zip(p, offs[q])))
             if rounding is None:
-                prod = W[q] * v
+                prod = wt(q, p) * v
                 acc = acc + prod
                 if require_representable and (_rnd(prod) != prod or _rnd(acc) != acc):
                     raise ArithmeticError("intermediate not representable")
             elif rounding == "fma":
-                acc = _rnd(W[q] * v + acc)
+                acc = _rnd(wt(q, p) * v + acc)
             else:
-                acc = _rnd(acc + _rnd(W[q] * v))
+                acc = _rnd(acc + _rnd(wt(q, p) * v))
         return acc
 
     for _ in range(T):

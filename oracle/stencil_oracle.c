@@ -38,6 +38,10 @@
  *                    the product and the sum each rounded.
  *    Built with -ffp-contract=off so that the compiler fuses nothing;
  *    fma() is the C99 correctly rounded fused multiply-add.
+ *  - Variable coefficients (Section 3.4 treats LCS's second sequence B as a
+ *    variable coefficient): when a coefficient field is given, the weight of
+ *    canonical term q at point p is field[q * N + p] (N = grid points)
+ *    instead of w[q]; everything else is unchanged.
  */
 #include <math.h>
 #include <stdint.h>
@@ -95,19 +99,28 @@ static double fetch(const double* u, const grid_t* g, int64_t i, int64_t j, int6
     return u[(i * g->n[1] + j) * g->n[2] + k];
 }
 
+/* Weight of canonical term q at point (i, j, k): w[q], or the field's value. */
+static double weight(const double* w, const double* field, const grid_t* g, int q, int64_t i, int64_t j, int64_t k)
+{
+    if (!field) return w[q];
+    int64_t n = g->n[0] * g->n[1] * g->n[2];
+    return field[q * n + (i * g->n[1] + j) * g->n[2] + k];
+}
+
 /* One point update: the weighted sum over the stencil in descending
  * canonical order, with the rounding of the chosen arithmetic mode. */
 static double update(const double* src, const grid_t* g, int64_t i, int64_t j, int64_t k,
-                     const int* off, const double* w, int K, int arith)
+                     const int* off, const double* w, const double* field, int K, int arith)
 {
     int q = K - 1;
-    double acc = w[q] * fetch(src, g, i + off[3 * q], j + off[3 * q + 1], k + off[3 * q + 2]);
+    double acc = weight(w, field, g, q, i, j, k) * fetch(src, g, i + off[3 * q], j + off[3 * q + 1], k + off[3 * q + 2]);
     for (q = K - 2; q >= 0; --q) {
         double v = fetch(src, g, i + off[3 * q], j + off[3 * q + 1], k + off[3 * q + 2]);
+        double wq = weight(w, field, g, q, i, j, k);
         if (arith == OR_ARITH_FMA) {
-            acc = fma(w[q], v, acc);
+            acc = fma(wq, v, acc);
         } else {
-            double prod = w[q] * v;
+            double prod = wq * v;
             acc = acc + prod;
         }
     }
@@ -115,10 +128,12 @@ static double update(const double* src, const grid_t* g, int64_t i, int64_t j, i
 }
 
 /* Advance u (C order, ext[0] slowest, interior points only) by T steps.
- * Returns 0, or -1 on invalid arguments. nthreads <= 0 uses the OpenMP
- * default; the result does not depend on the thread count. */
-int oracle_run(int dim, int shape, int r, const double* w, int K, int method, int bc, double c,
-               int arith, const int64_t* ext, int64_t T, double* u, int nthreads)
+ * field: NULL for the constant weights w, else K * N per-point weights
+ * (term-major, canonical order). Returns 0, or -1 on invalid arguments.
+ * nthreads <= 0 uses the OpenMP default; the result does not depend on the
+ * thread count. */
+int oracle_run_field(int dim, int shape, int r, const double* w, const double* field, int K, int method, int bc,
+                     double c, int arith, const int64_t* ext, int64_t T, double* u, int nthreads)
 {
     int off[3 * 729];
     if (r > 4) return -1;
@@ -151,7 +166,7 @@ int oracle_run(int dim, int shape, int r, const double* w, int K, int method, in
             for (int64_t i = 0; i < g.n[0]; ++i)
                 for (int64_t j = 0; j < g.n[1]; ++j)
                     for (int64_t k = 0; k < g.n[2]; ++k)
-                        b[(i * g.n[1] + j) * g.n[2] + k] = update(a, &g, i, j, k, off, w, K, arith);
+                        b[(i * g.n[1] + j) * g.n[2] + k] = update(a, &g, i, j, k, off, w, field, K, arith);
             double* s = a; a = b; b = s;
         }
         if (a != u) memcpy(u, a, (size_t)total * sizeof(double));
@@ -161,11 +176,17 @@ int oracle_run(int dim, int shape, int r, const double* w, int K, int method, in
             for (int64_t i = 0; i < g.n[0]; ++i)
                 for (int64_t j = 0; j < g.n[1]; ++j)
                     for (int64_t k = 0; k < g.n[2]; ++k)
-                        u[(i * g.n[1] + j) * g.n[2] + k] = update(u, &g, i, j, k, off, w, K, arith);
+                        u[(i * g.n[1] + j) * g.n[2] + k] = update(u, &g, i, j, k, off, w, field, K, arith);
     } else {
         return -1;
     }
     return 0;
+}
+
+int oracle_run(int dim, int shape, int r, const double* w, int K, int method, int bc, double c,
+               int arith, const int64_t* ext, int64_t T, double* u, int nthreads)
+{
+    return oracle_run_field(dim, shape, r, w, NULL, K, method, bc, c, arith, ext, T, u, nthreads);
 }
 
 int oracle_max_threads(void)

@@ -26,10 +26,13 @@ MUTANTS = {
                           "for (int64_t k = g.n[2] - 1; k >= 0; --k)\n                        u[")],
     "periodic_as_constant": [("if (g->bc == OR_BC_PERIODIC) {", "if (0) {")],
     "halo_zero": [("return g->c;", "return 0.0;")],
-    "fma_mode_unfused": [("acc = fma(w[q], v, acc);", "acc = acc + w[q] * v;")],
-    "unfused_mode_fused": [("double prod = w[q] * v;\n            acc = acc + prod;", "acc = fma(w[q], v, acc);")],
+    "fma_mode_unfused": [("acc = fma(wq, v, acc);", "acc = acc + wq * v;")],
+    "unfused_mode_fused": [("double prod = wq * v;\n            acc = acc + prod;", "acc = fma(wq, v, acc);")],
     "jacobi_in_place": [("b[(i * g.n[1] + j) * g.n[2] + k] = update(a,", "a[(i * g.n[1] + j) * g.n[2] + k] = update(a,")],
     "star_has_corners": [("if (shape == OR_STAR && nz > 1) continue;", "if (shape == OR_STAR && nz > 2) continue;")],
+    "field_point_shifted": [("* g->n[2] + k];", "* g->n[2] + (k + 1) % g->n[2]];")],
+    "field_terms_swapped": [("return field[q * n +", "return field[(q == 0 ? 1 : (q == 1 ? 0 : q)) * n +")],
+    "field_ignored": [("if (!field) return w[q];", "return w[q];")],
     "one_step_too_many": [("for (int64_t t = 0; t < T; ++t) {", "for (int64_t t = 0; t <= T; ++t) {")],
 }
 
@@ -63,6 +66,17 @@ def _quick_pins(lib):
                                            c=0.1, rounding=rounding), (5, 6))
             got = orc(u0, 2, dim=2, shape=oracle.STAR, r=1, weights=w, method=method, c=0.1, arith=arith)
             assert np.array_equal(got, ref), ("P1b", mname, rounding)
+    # per-point weights: rounding emulation with a coefficient field
+    for dim, shape, ext in ((2, "box", (4, 5)), (3, "star", (3, 4, 4))):
+        k = len(exact.canonical_offsets(dim, shape, 1))
+        field = inputs.uniform(60 + dim, k * int(np.prod(ext))).reshape((k,) + ext) / k
+        u0 = inputs.grid(61 + dim, ext)
+        for mname, method in (("jacobi", oracle.JACOBI), ("gs", oracle.GAUSS_SEIDEL)):
+            ref = exact.to_array(exact.run(u0, 2, dim=dim, shape=shape, r=1, weights=[0.0] * k, method=mname,
+                                           c=0.3, rounding="fma", field=field), ext)
+            got = orc(u0, 2, dim=dim, shape=oracle.STAR if shape == "star" else oracle.BOX, r=1,
+                      weights=[0.0] * k, method=method, c=0.3, field=field)
+            assert np.array_equal(got, ref), ("field", dim, mname)
     # P2: Fourier decay, periodic Jacobi
     ext = (16, 24)
     offs = exact.canonical_offsets(2, "box", 1)

@@ -248,3 +248,46 @@ def test_rejects_bad_arguments():
         oracle.run(u, -1, dim=1, shape=oracle.STAR, r=1, weights=[1, 1, 1])
     got = oracle.run(u + 0.5, 0, dim=1, shape=oracle.STAR, r=1, weights=[1, 1, 1])
     assert np.array_equal(got, u + 0.5)
+
+
+# ---- variable coefficients (a per-point weight field) -------------------------------------------
+
+@pytest.mark.parametrize("dim,shape,ext", [(1, "star", (11,)), (2, "star", (5, 6)), (2, "box", (4, 5)),
+                                           (3, "star", (3, 4, 4))])
+@pytest.mark.parametrize("method", ["jacobi", "gs"])
+@pytest.mark.parametrize("bc", ["constant", "periodic"])
+def test_pvar_field_rounding_emulated(dim, shape, ext, method, bc):
+    """Per-point weights: every rounding reproduced by the independent Fraction implementation."""
+    offs = exact.canonical_offsets(dim, shape, 1)
+    k = len(offs)
+    field = inputs.uniform(401 + dim, k * int(np.prod(ext))).reshape((k,) + ext) / k
+    u0 = inputs.grid(402 + dim, ext)
+    for rounding, arith in (("fma", oracle.ARITH_FMA), ("unfused", oracle.ARITH_UNFUSED)):
+        ref = exact.to_array(exact.run(u0, 2, dim=dim, shape=shape, r=1, weights=[0.0] * k, method=method, bc=bc,
+                                       c=0.2, rounding=rounding, field=field), ext)
+        got = oracle.run(u0, 2, dim=dim, shape=SHAPES[shape], r=1, weights=[0.0] * k, method=METHODS[method],
+                         bc=BCS[bc], c=0.2, arith=arith, field=field)
+        assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("method", [oracle.JACOBI, oracle.GAUSS_SEIDEL])
+def test_pvar_uniform_field_equals_constant_weights(method):
+    """A field that repeats the constant weights at every point gives the constant-weight result bit for bit."""
+    w = inputs.normalized_weights(77, 9)
+    u0 = inputs.grid(78, (13, 17))
+    field = np.broadcast_to(np.asarray(w).reshape(9, 1, 1), (9, 13, 17)).copy()
+    a = oracle.run(u0, 5, dim=2, shape=oracle.BOX, r=1, weights=w, method=method, c=0.4)
+    b = oracle.run(u0, 5, dim=2, shape=oracle.BOX, r=1, weights=[0.0] * 9, method=method, c=0.4, field=field)
+    assert np.array_equal(a, b)
+
+
+def test_pvar_field_is_really_per_point():
+    """Changing the weight of one point changes that point's first update and nothing else at T = 1 (Jacobi)."""
+    w = inputs.normalized_weights(79, 3)
+    u0 = inputs.grid(80, (20,))
+    field = np.broadcast_to(np.asarray(w).reshape(3, 1), (3, 20)).copy()
+    base = oracle.run(u0, 1, dim=1, shape=oracle.STAR, r=1, weights=w, field=field)
+    field[1, 7] *= 0.5
+    changed = oracle.run(u0, 1, dim=1, shape=oracle.STAR, r=1, weights=w, field=field)
+    diff = np.nonzero(base != changed)[0]
+    assert list(diff) == [7]
