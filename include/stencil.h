@@ -140,6 +140,28 @@ int stencil_run(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_s
 int stencil_run_batch(const stencil_handle* h, const stencil_grid* g, const int64_t* T, int n,
                       void* cuda_stream);
 
+/*
+ * Bind per-point coefficients: a variable-coefficient stencil, the form in
+ * which Section 3.4 treats LCS's second sequence (its value at a point acts
+ * as that point's coefficient). Runs of h then compute
+ *     u'[p] = sum_o f_o[p] * u[B(p + o)]
+ * with the same terms, order and rounding as with constant coefficients.
+ *   field  DEVICE pointer to K * N doubles (8-byte aligned), N = ext[0] * ...
+ *          * ext[dim-1]: the weight of canonical term q (0 <= q < K) at grid
+ *          point p (C order) is field[q * N + p]. NULL unbinds it and
+ *          restores the constant coefficients of stencil_create.
+ *   ext    extents of the grids the field belongs to; a run of h on a grid of
+ *          other extents returns STENCIL_EINVAL while the field is bound.
+ * Not copied: the caller keeps the field allocated and unchanged until every
+ * run that reads it has finished; the pointer is read at each run, so a
+ * field rebound between runs of a captured batch makes a new graph.
+ * Kernel families: Jacobi runs use the plain kernel (a BLOCKED plan returns
+ * STENCIL_EUNSUPPORTED); Gauss-Seidel runs use the wavefront or plain sweeps
+ * as with constant coefficients; in stencil_run_batch a problem with a field
+ * runs as its own launches. Returns STENCIL_OK or STENCIL_EINVAL.
+ */
+int stencil_set_coeff_field(stencil_handle h, const double* field, const int64_t ext[3]);
+
 /* Bytes of workspace stencil_run needs for g (0 for Gauss-Seidel). */
 int stencil_workspace_bytes(stencil_handle h, const stencil_grid* g, size_t* bytes);
 

@@ -48,6 +48,7 @@ static int check_grid(const stencil_handle_s* h, const stencil_grid* g)
     for (int d = 0; d < h->dim; ++d) {
         if (g->ext[d] < 1) return STENCIL_EINVAL;
         if (h->bc == STENCIL_BC_PERIODIC && g->ext[d] < 2 * h->r + 1) return STENCIL_EINVAL;
+        if (h->field && g->ext[d] != h->field_ext[d]) return STENCIL_EINVAL;
     }
     int64_t n = 1;
     for (int d = 0; d < h->dim; ++d) {
@@ -127,6 +128,25 @@ int stencil_set_plan(stencil_handle h, int kernel, int tb, const int64_t tile[3]
     return STENCIL_OK;
 }
 
+int stencil_set_coeff_field(stencil_handle h, const double* field, const int64_t ext[3])
+{
+    if (!h) return STENCIL_EINVAL;
+    if (!field) {
+        h->field = nullptr;
+        for (int d = 0; d < 3; ++d) h->field_ext[d] = 0;
+        return STENCIL_OK;
+    }
+    if (!ext || ((uintptr_t)field & 7)) return STENCIL_EINVAL;
+    int64_t n = 1;
+    for (int d = 0; d < h->dim; ++d) {
+        if (ext[d] < 1 || n > INT64_MAX / ext[d] / 8 / h->K) return STENCIL_EINVAL;
+        n *= ext[d];
+    }
+    h->field = field;
+    for (int d = 0; d < 3; ++d) h->field_ext[d] = d < h->dim ? ext[d] : 0;
+    return STENCIL_OK;
+}
+
 int stencil_workspace_bytes(stencil_handle h, const stencil_grid* g, size_t* bytes)
 {
     if (!bytes) return STENCIL_EINVAL;
@@ -146,7 +166,7 @@ int stencil_run(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_s
     ctx.h = h;
     ctx.g = make_geo(h->dim, g->ext);
     ctx.st = (cudaStream_t)cuda_stream;
-    ctx.sd = StencilDev{h->K, h->r, h->bc, h->arith, h->c, h->d_w, h->d_off, h->d_status};
+    ctx.sd = make_sd(h, npoints(h->dim, g->ext));
     const size_t bytes = (size_t)npoints(h->dim, g->ext) * sizeof(double);
 
     if (h->method == STENCIL_GAUSS_SEIDEL) {

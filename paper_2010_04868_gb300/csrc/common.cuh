@@ -9,6 +9,11 @@
 //   ARITH_UNFUSED  acc = w0*v0 (rounded), then acc = acc + (wq*vq), each rounded
 // The intrinsics __dmul_rn / __fma_rn / __dadd_rn pin every rounding; the
 // compiler never contracts them.
+//
+// Weights come from a weight source: WArr (the same K weights at every point)
+// or WField (per-point weights, a variable-coefficient stencil as Section 3.4
+// treats LCS's second sequence). Both answer at(q, p), the weight of the q-th
+// term in summation order at the point of linear index p.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -35,6 +40,8 @@ struct StencilDev {
     const double* w;   // K weights, descending canonical order (device)
     const int* off;    // 3K offset components, descending canonical order (device)
     int* status;       // device status word
+    const double* field;  // per-point weights (canonical term-major, K x npts) or nullptr
+    int64_t npts;         // points of the grid the field belongs to
 };
 
 __host__ __device__ constexpr int stencil_k(int dim, int shape, int r)
@@ -88,7 +95,27 @@ struct Stn {
 
 template <int K>
 struct WArr {
+    static constexpr bool per_point = false;
     double w[K];  // descending canonical order
+    __device__ __forceinline__ double at(int q, int64_t) const { return w[q]; }
+};
+
+// The same weights at every point, read from memory (shared or global).
+struct WPtr {
+    static constexpr bool per_point = false;
+    const double* w;
+    __device__ __forceinline__ double at(int q, int64_t) const { return w[q]; }
+};
+
+// Per-point weights: f holds K planes of n doubles in CANONICAL term order, so
+// the q-th term in summation (descending) order is plane K-1-q. Read through
+// the non-coherent path: no kernel writes the field.
+template <int K>
+struct WField {
+    static constexpr bool per_point = true;
+    const double* f;
+    int64_t n;
+    __device__ __forceinline__ double at(int q, int64_t p) const { return __ldg(f + (int64_t)(K - 1 - q) * n + p); }
 };
 
 template <int ARITH>
@@ -120,26 +147,26 @@ __device__ __forceinline__ double fetch_bc(const double* u, int64_t i, int64_t j
     return u[(i * g.n1 + j) * g.n2 + k];
 }
 
-// Full update at (i, j, k) with compile-time offsets and the boundary rule
-// applied to every term.
-template <int DIM, int SHAPE, int R, int ARITH>
+// Full update at (i, j, k) (inside the grid) with compile-time offsets and
+// the boundary rule applied to every term.
+template <int DIM, int SHAPE, int R, int ARITH, class WS>
 __device__ __forceinline__ double update_bc(const double* u, int64_t i, int64_t j, int64_t k, const Geo& g,
-                                            int bc, double c, const double* w)
+                                            int bc, double c, const WS& w)
 {
     using S = Stn<DIM, SHAPE, R>;
+    const int64_t p = (i * g.n1 + j) * g.n2 + k;
     double v[S::K];
 #pragma unroll
     for (int q = 0; q < S::K; ++q) v[q] = fetch_bc(u, i + S::o(q, 0), j + S::o(q, 1), k + S::o(q, 2), g, bc, c);
-    double acc = __dmul_rn(w[0], v[0]);
+    double acc = __dmul_rn(w.at(0, p), v[0]);
 #pragma unroll
-    for (int q = 1; q < S::K; ++q) acc = acc_step<ARITH>(acc, w[q], v[q]);
+    for (int q = 1; q < S::K; ++q) acc = acc_step<ARITH>(acc, w.at(q, p), v[q]);
     return acc;
 }
 
 // Full update at linear index p whose every neighbour is inside the grid.
-template <int DIM, int SHAPE, int R, int ARITH, bool RO>
-__device__ __forceinline__ double update_interior(const double* u, int64_t p, int64_t s0, int64_t s1,
-                                                  const double* w)
+template <int DIM, int SHAPE, int R, int ARITH, bool RO, class WS>
+__device__ __forceinline__ double update_interior(const double* u, int64_t p, int64_t s0, int64_t s1, const WS& w)
 {
     using S = Stn<DIM, SHAPE, R>;
     double v[S::K];
@@ -148,9 +175,9 @@ __device__ __forceinline__ double update_interior(const double* u, int64_t p, in
         const double* a = u + p + S::o(q, 0) * s0 + S::o(q, 1) * s1 + S::o(q, 2);
         v[q] = RO ? __ldg(a) : *a;
     }
-    double acc = __dmul_rn(w[0], v[0]);
+    double acc = __dmul_rn(w.at(0, p), v[0]);
 #pragma unroll
-    for (int q = 1; q < S::K; ++q) acc = acc_step<ARITH>(acc, w[q], v[q]);
+    for (int q = 1; q < S::K; ++q) acc = acc_step<ARITH>(acc, w.at(q, p), v[q]);
     return acc;
 }
 
@@ -168,7 +195,7 @@ __device__ __forceinline__ double update_rt(const double* u, int64_t i, int64_t 
             int q = q0 + t;
             if (q < s.K) {
                 v[t] = fetch_bc(u, i + s.off[3 * q], j + s.off[3 * q + 1], k + s.off[3 * q + 2], g, s.bc, s.c);
-                w[t] = s.w[q];
+                w[t] = s.field ? __ldg(s.field + (int64_t)(s.K - 1 - q) * s.npts + (i * g.n1 + j) * g.n2 + k) : s.w[q];
             }
         }
 #pragma unroll

@@ -27,6 +27,10 @@ struct stencil_handle_s {
     // after debug_spin polls instead of the default limit
     int64_t debug_stall_tile = -1;
     int debug_spin = 0;
+    // per-point weights bound by stencil_set_coeff_field (caller-owned device
+    // memory, canonical term-major) and the extents of the grids they belong to
+    const double* field = nullptr;
+    int64_t field_ext[3] = {0, 0, 0};
     int plan_kernel = STENCIL_KERNEL_AUTO;
     int plan_tb = 0;
     int64_t plan_tile[3] = {0, 0, 0};
@@ -45,6 +49,12 @@ struct RunCtx {
 };
 
 inline int cuda_rc(cudaError_t e) { return e == cudaSuccess ? STENCIL_OK : STENCIL_ECUDA; }
+
+// Device-side description of h for a grid of npts points (the bound field, if any).
+inline StencilDev make_sd(const stencil_handle_s* h, int64_t npts)
+{
+    return StencilDev{h->K, h->r, h->bc, h->arith, h->c, h->d_w, h->d_off, h->d_status, h->field, npts};
+}
 
 // True if the plain kernels have a compile-time specialisation for (dim, shape, r).
 bool plain_specialised(int dim, int shape, int r);

@@ -218,8 +218,8 @@ __device__ __noinline__ void unit_jplain_sp(const BProb& P, int64_t ph, int64_t 
     for_jacobi_unit<!(DIM == 3 && SHAPE == BOX)>(P, u, [&](int64_t i, int64_t j, int64_t k, int64_t p) {
         const bool in = (DIM < 3 || (i >= 1 && i < P.g.n0 - 1)) && (DIM < 2 || (j >= 1 && j < P.g.n1 - 1)) &&
                         k >= 1 && k < P.g.n2 - 1;
-        dst[p] = in ? update_interior<DIM, SHAPE, 1, ARITH, false>(src, p, s0, s1, sw)
-                    : update_bc<DIM, SHAPE, 1, ARITH>(src, i, j, k, P.g, P.bc, P.c, sw);
+        dst[p] = in ? update_interior<DIM, SHAPE, 1, ARITH, false>(src, p, s0, s1, WPtr{sw})
+                    : update_bc<DIM, SHAPE, 1, ARITH>(src, i, j, k, P.g, P.bc, P.c, WPtr{sw});
     });
 }
 
@@ -328,8 +328,8 @@ __device__ __noinline__ void unit_gstile(const BProb& P, int64_t ph, int64_t uni
             const int64_t p = i * s0 + j * s1 + k;
             double r;
             if (SPEC)
-                r = (in01 && k >= 1 && k < P.g.n2 - 1) ? update_interior<DIM, SHAPE, 1, ARITH, false>(u, p, s0, s1, sw)
-                                                       : update_bc<DIM, SHAPE, 1, ARITH>(u, i, j, k, P.g, P.bc, P.c, sw);
+                r = (in01 && k >= 1 && k < P.g.n2 - 1) ? update_interior<DIM, SHAPE, 1, ARITH, false>(u, p, s0, s1, WPtr{sw})
+                                                       : update_bc<DIM, SHAPE, 1, ARITH>(u, i, j, k, P.g, P.bc, P.c, WPtr{sw});
             else
                 r = point_bc<ARITH>(u, i, j, k, P, sw, so);
             u[p] = r;
@@ -599,7 +599,8 @@ int batch_run(const stencil_handle* hs, const stencil_grid* gs, const int64_t* T
         const bool wave = h->method == GAUSS_SEIDEL && h->bc == BC_CONSTANT &&
                           plans[i].kernel == STENCIL_KERNEL_WAVEFRONT &&
                           gs_wavefront_supported(h, make_geo(h->dim, gs[i].ext));
-        if (!wave && h->K <= BMAXK && describe(h, &gs[i], Ts[i], plans[i], P)) {
+        // per-point weights: the problem runs as its own launches (the shared kernel reads constant weights)
+        if (!wave && !h->field && h->K <= BMAXK && describe(h, &gs[i], Ts[i], plans[i], P)) {
             P.spec = spec_of(h);
             if (P.kind == BK_GSTILE && h->dim == 1) P.spec = SP_NONE;
             inside.push_back(i);
@@ -613,8 +614,8 @@ int batch_run(const stencil_handle* hs, const stencil_grid* gs, const int64_t* T
     {
         char buf[256];
         for (int i = 0; i < n; ++i) {
-            snprintf(buf, sizeof buf, "%p,%p,%p,%lld,%lld,%lld,%lld,%d,%d,%lld,%lld,%lld;", (void*)hs[i],
-                     (void*)gs[i].data, (void*)gs[i].scratch, (long long)gs[i].ext[0], (long long)gs[i].ext[1],
+            snprintf(buf, sizeof buf, "%p,%p,%p,%p,%lld,%lld,%lld,%lld,%d,%d,%lld,%lld,%lld;", (void*)hs[i],
+                     (const void*)hs[i]->field, (void*)gs[i].data, (void*)gs[i].scratch, (long long)gs[i].ext[0], (long long)gs[i].ext[1],
                      (long long)gs[i].ext[2], (long long)Ts[i], plans[i].kernel, plans[i].tb,
                      (long long)plans[i].tile[0], (long long)plans[i].tile[1], (long long)plans[i].tile[2]);
             key += buf;

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256) k_jacobi_blocked(const __grid_constant__ 
                 if (i < 0 || i >= g.n0 || j < 0 || j >= g.n1 || k < 0 || k >= g.n2) continue;
             }
             const int64_t p = s0 * st0 + s1 * st1 + s2;
-            dst[p] = update_interior<DIM, SHAPE, R, ARITH, false>(src, p, st0, st1, w.w);
+            dst[p] = update_interior<DIM, SHAPE, R, ARITH, false>(src, p, st0, st1, w);
         }
         __syncthreads();
         double* tmp = src;
@@ -211,7 +211,8 @@ static EncodeTiledFn encode_fn()
 bool jacobi_blocked_supported(const stencil_handle_s* h, const Geo& g)
 {
     (void)g;
-    return h->method == JACOBI && plain_specialised(h->dim, h->shape, h->r) &&
+    // constant weights only: the staged tile has no room for K weight planes
+    return h->method == JACOBI && !h->field && plain_specialised(h->dim, h->shape, h->r) &&
            !(h->dim == 3 && h->shape == BOX && h->r == 2);
 }
 

@@ -63,6 +63,7 @@ extern "C" int stencil_run_noalloc(stencil_handle h, const stencil_grid* g, int6
     for (int d = 0; d < h->dim; ++d) {
         if (g->ext[d] < 1) return STENCIL_EINVAL;
         if (h->bc == STENCIL_BC_PERIODIC && g->ext[d] < 2 * h->r + 1) return STENCIL_EINVAL;
+        if (h->field && g->ext[d] != h->field_ext[d]) return STENCIL_EINVAL;
         if (n > NOALLOC_MAX_POINTS) return STENCIL_EUNSUPPORTED;
         n *= g->ext[d];
     }
@@ -78,7 +79,7 @@ extern "C" int stencil_run_noalloc(stencil_handle h, const stencil_grid* g, int6
     ctx.h = h;
     ctx.g = make_geo(h->dim, g->ext);
     ctx.st = (cudaStream_t)cuda_stream;
-    ctx.sd = StencilDev{h->K, h->r, h->bc, h->arith, h->c, h->d_w, h->d_off, h->d_status};
+    ctx.sd = make_sd(h, n);
     double* a = g->data;
     double* b = scratch;
     for (int64_t t = 0; t < T; ++t) {

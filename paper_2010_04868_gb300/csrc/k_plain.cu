@@ -51,17 +51,31 @@ bool plain_specialised(int dim, int shape, int r)
 // Points per thread along the blocked axis (axis 1 in 2D, axis 0 in 3D): the
 // unrolled points give each thread independent FMA chains, let their loads
 // issue early and share the neighbour rows they have in common.
-template <int DIM, int K>
+// With per-point weights (FIELD) every point also streams K weights from
+// HBM: one point per thread and more resident warps hide that latency
+// better than several points per thread (measured on 4096^2 5-point and
+// 256^3 7-point grids: 63 -> 85 and 48 -> 52 GStencil/s).
+constexpr int PLAIN_FIELD_RB2 = 1, PLAIN_FIELD_RB3 = 1;
+constexpr int PLAIN_FIELD_MINB2 = 3, PLAIN_FIELD_MINB3 = 4;
+
+template <int DIM, int K, bool FIELD = false>
 __host__ __device__ constexpr int plain_rb()
 {
-    return DIM == 1 ? 1 : (DIM == 2 ? (K <= 9 ? 4 : 2) : 2);
+    return DIM == 1 ? 1
+                    : (DIM == 2 ? (FIELD ? PLAIN_FIELD_RB2 : (K <= 9 ? 4 : 2)) : (FIELD ? PLAIN_FIELD_RB3 : 2));
 }
 
-template <int DIM, int SHAPE, int R, int ARITH>
-__global__ void __launch_bounds__(256, DIM == 3 ? 3 : 1) k_jacobi_plain(const double* __restrict__ u, double* __restrict__ v, Geo g,
-                                                      int bc, double c, WArr<Stn<DIM, SHAPE, R>::K> w)
+template <int DIM, bool FIELD>
+__host__ __device__ constexpr int plain_minb()
 {
-    constexpr int RB = plain_rb<DIM, Stn<DIM, SHAPE, R>::K>();
+    return DIM == 3 ? (FIELD ? PLAIN_FIELD_MINB3 : 3) : (FIELD ? PLAIN_FIELD_MINB2 : 1);
+}
+
+template <int DIM, int SHAPE, int R, int ARITH, class WS>
+__global__ void __launch_bounds__(256, plain_minb<DIM, WS::per_point>()) k_jacobi_plain(const double* __restrict__ u,
+                                                      double* __restrict__ v, Geo g, int bc, double c, WS w)
+{
+    constexpr int RB = plain_rb<DIM, Stn<DIM, SHAPE, R>::K, WS::per_point>();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n2) return;
     const int64_t s1 = g.n2, s0 = g.n1 * g.n2;
@@ -77,8 +91,8 @@ __global__ void __launch_bounds__(256, DIM == 3 ? 3 : 1) k_jacobi_plain(const do
                     if (i < g.n0) {
                         const int64_t p = i * s0 + j * s1 + k;
                         const bool in = kin && jin && i >= R && i < g.n0 - R;
-                        v[p] = in ? update_interior<DIM, SHAPE, R, ARITH, true>(u, p, s0, s1, w.w)
-                                  : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w.w);
+                        v[p] = in ? update_interior<DIM, SHAPE, R, ARITH, true>(u, p, s0, s1, w)
+                                  : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w);
                     }
                 }
             }
@@ -91,8 +105,8 @@ __global__ void __launch_bounds__(256, DIM == 3 ? 3 : 1) k_jacobi_plain(const do
                 if (j < g.n1) {
                     const int64_t p = j * s1 + k;
                     const bool in = kin && (DIM < 2 || (j >= R && j < g.n1 - R));
-                    v[p] = in ? update_interior<DIM, SHAPE, R, ARITH, true>(u, p, s0, s1, w.w)
-                              : update_bc<DIM, SHAPE, R, ARITH>(u, 0, j, k, g, bc, c, w.w);
+                    v[p] = in ? update_interior<DIM, SHAPE, R, ARITH, true>(u, p, s0, s1, w)
+                              : update_bc<DIM, SHAPE, R, ARITH>(u, 0, j, k, g, bc, c, w);
                 }
             }
         }
@@ -122,13 +136,11 @@ static void plain_launch_shape(const Geo& g, dim3& grid, dim3& block)
     grid = dim3((unsigned)gx, (unsigned)(gy < 65535 ? gy : 65535), (unsigned)(g.n0 < 65535 ? g.n0 : 65535));
 }
 
-template <int DIM, int SHAPE, int R>
-static void launch_jacobi_plain(const RunCtx& ctx, const double* in, double* out)
+template <int DIM, int SHAPE, int R, class WS>
+static void launch_jacobi_plain(const RunCtx& ctx, const double* in, double* out, const WS& w)
 {
     constexpr int K = Stn<DIM, SHAPE, R>::K;
-    constexpr int RB = plain_rb<DIM, K>();
-    WArr<K> w;
-    for (int q = 0; q < K; ++q) w.w[q] = ctx.h->w_desc[q];
+    constexpr int RB = plain_rb<DIM, K, WS::per_point>();
     dim3 grid, block;
     plain_launch_shape(ctx.g, grid, block);
     if (DIM == 3) {
@@ -139,9 +151,22 @@ static void launch_jacobi_plain(const RunCtx& ctx, const double* in, double* out
         grid.y = (unsigned)(gy < 65535 ? gy : 65535);
     }
     if (ctx.h->arith == ARITH_FMA)
-        k_jacobi_plain<DIM, SHAPE, R, ARITH_FMA><<<grid, block, 0, ctx.st>>>(in, out, ctx.g, ctx.h->bc, ctx.h->c, w);
+        k_jacobi_plain<DIM, SHAPE, R, ARITH_FMA, WS><<<grid, block, 0, ctx.st>>>(in, out, ctx.g, ctx.h->bc, ctx.h->c, w);
     else
-        k_jacobi_plain<DIM, SHAPE, R, ARITH_UNFUSED><<<grid, block, 0, ctx.st>>>(in, out, ctx.g, ctx.h->bc, ctx.h->c, w);
+        k_jacobi_plain<DIM, SHAPE, R, ARITH_UNFUSED, WS><<<grid, block, 0, ctx.st>>>(in, out, ctx.g, ctx.h->bc, ctx.h->c, w);
+}
+
+template <int DIM, int SHAPE, int R>
+static void launch_jacobi_plain(const RunCtx& ctx, const double* in, double* out)
+{
+    constexpr int K = Stn<DIM, SHAPE, R>::K;
+    if (ctx.sd.field) {
+        launch_jacobi_plain<DIM, SHAPE, R>(ctx, in, out, WField<K>{ctx.sd.field, ctx.sd.npts});
+    } else {
+        WArr<K> w;
+        for (int q = 0; q < K; ++q) w.w[q] = ctx.h->w_desc[q];
+        launch_jacobi_plain<DIM, SHAPE, R>(ctx, in, out, w);
+    }
 }
 
 int jacobi_plain_step(const RunCtx& ctx, const double* in, double* out)
@@ -174,8 +199,8 @@ int jacobi_plain_step(const RunCtx& ctx, const double* in, double* out)
 // Indices that fall outside the grid read c (constant) or wrap (periodic);
 // a right neighbour that wraps lands on an index this sweep has already
 // updated, so it is read back from memory.
-template <int R, int ARITH>
-__global__ void k_gs1d_serial(double* u, int64_t n, int bc, double c, WArr<2 * R + 1> w)
+template <int R, int ARITH, class WS>
+__global__ void k_gs1d_serial(double* u, int64_t n, int bc, double c, WS w)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     auto fetch = [&](int64_t x) -> double {
@@ -188,9 +213,9 @@ __global__ void k_gs1d_serial(double* u, int64_t n, int bc, double c, WArr<2 * R
     for (int m = 0; m <= 2 * R; ++m) win[m] = fetch(m - R);
     for (int64_t x = 0; x < n; ++x) {
         // descending canonical order: offsets +R .. -R, i.e. win[2R] .. win[0]
-        double acc = __dmul_rn(w.w[0], win[2 * R]);
+        double acc = __dmul_rn(w.at(0, x), win[2 * R]);
 #pragma unroll
-        for (int q = 1; q <= 2 * R; ++q) acc = acc_step<ARITH>(acc, w.w[q], win[2 * R - q]);
+        for (int q = 1; q <= 2 * R; ++q) acc = acc_step<ARITH>(acc, w.at(q, x), win[2 * R - q]);
         u[x] = acc;
 #pragma unroll
         for (int m = 0; m < 2 * R; ++m) win[m] = win[m + 1];
@@ -229,9 +254,8 @@ struct TileGS {
 
 // One tile diagonal D. Threads own the (i, j) lines of a tile (2D: j) and
 // walk theta, one CTA barrier per theta.
-template <int DIM, int SHAPE, int R, int ARITH>
-__global__ void __launch_bounds__(256) k_gs_tile(double* u, Geo g, int bc, double c,
-                                                 WArr<Stn<DIM, SHAPE, R>::K> w, TileGS t, int64_t D)
+template <int DIM, int SHAPE, int R, int ARITH, class WS>
+__global__ void __launch_bounds__(256) k_gs_tile(double* u, Geo g, int bc, double c, WS w, TileGS t, int64_t D)
 {
     int64_t T0, T1;
     if (DIM == 3) {
@@ -255,20 +279,17 @@ __global__ void __launch_bounds__(256) k_gs_tile(double* u, Geo g, int bc, doubl
         const int64_t k = kb + ls;
         if (owner && k >= 0 && k < g.n2) {
             const int64_t p = i * s0 + j * s1 + k;
-            double r = (in01 && k >= R && k < g.n2 - R) ? update_interior<DIM, SHAPE, R, ARITH, false>(u, p, s0, s1, w.w)
-                                                        : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w.w);
+            double r = (in01 && k >= R && k < g.n2 - R) ? update_interior<DIM, SHAPE, R, ARITH, false>(u, p, s0, s1, w)
+                                                        : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w);
             u[p] = r;
         }
         __syncthreads();
     }
 }
 
-template <int DIM, int SHAPE, int R>
-static int gs_tiles(const RunCtx& ctx, double* u, int64_t T)
+template <int DIM, int SHAPE, int R, class WS>
+static int gs_tiles(const RunCtx& ctx, double* u, int64_t T, const WS& w)
 {
-    constexpr int K = Stn<DIM, SHAPE, R>::K;
-    WArr<K> w;
-    for (int q = 0; q < K; ++q) w.w[q] = ctx.h->w_desc[q];
     const Geo& g = ctx.g;
     const bool box = SHAPE == BOX;
     TileGS t;
@@ -290,9 +311,9 @@ static int gs_tiles(const RunCtx& ctx, double* u, int64_t T)
     for (int64_t s = 0; s < T; ++s)
         for (int64_t D = 0; D <= Dmax; ++D) {
             if (ctx.h->arith == ARITH_FMA)
-                k_gs_tile<DIM, SHAPE, R, ARITH_FMA><<<nblk, nthr, 0, ctx.st>>>(u, g, ctx.h->bc, ctx.h->c, w, t, D);
+                k_gs_tile<DIM, SHAPE, R, ARITH_FMA, WS><<<nblk, nthr, 0, ctx.st>>>(u, g, ctx.h->bc, ctx.h->c, w, t, D);
             else
-                k_gs_tile<DIM, SHAPE, R, ARITH_UNFUSED><<<nblk, nthr, 0, ctx.st>>>(u, g, ctx.h->bc, ctx.h->c, w, t, D);
+                k_gs_tile<DIM, SHAPE, R, ARITH_UNFUSED, WS><<<nblk, nthr, 0, ctx.st>>>(u, g, ctx.h->bc, ctx.h->c, w, t, D);
             g_launches++;
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return STENCIL_ECUDA;
@@ -300,20 +321,37 @@ static int gs_tiles(const RunCtx& ctx, double* u, int64_t T)
     return STENCIL_OK;
 }
 
-template <int R>
-static int gs_1d(const RunCtx& ctx, double* u, int64_t T)
+template <int DIM, int SHAPE, int R>
+static int gs_tiles(const RunCtx& ctx, double* u, int64_t T)
 {
-    WArr<2 * R + 1> w;
-    for (int q = 0; q < 2 * R + 1; ++q) w.w[q] = ctx.h->w_desc[q];
+    constexpr int K = Stn<DIM, SHAPE, R>::K;
+    if (ctx.sd.field) return gs_tiles<DIM, SHAPE, R>(ctx, u, T, WField<K>{ctx.sd.field, ctx.sd.npts});
+    WArr<K> w;
+    for (int q = 0; q < K; ++q) w.w[q] = ctx.h->w_desc[q];
+    return gs_tiles<DIM, SHAPE, R>(ctx, u, T, w);
+}
+
+template <int R, class WS>
+static int gs_1d(const RunCtx& ctx, double* u, int64_t T, const WS& w)
+{
     for (int64_t s = 0; s < T; ++s) {
         if (ctx.h->arith == ARITH_FMA)
-            k_gs1d_serial<R, ARITH_FMA><<<1, 32, 0, ctx.st>>>(u, ctx.g.n2, ctx.h->bc, ctx.h->c, w);
+            k_gs1d_serial<R, ARITH_FMA, WS><<<1, 32, 0, ctx.st>>>(u, ctx.g.n2, ctx.h->bc, ctx.h->c, w);
         else
-            k_gs1d_serial<R, ARITH_UNFUSED><<<1, 32, 0, ctx.st>>>(u, ctx.g.n2, ctx.h->bc, ctx.h->c, w);
+            k_gs1d_serial<R, ARITH_UNFUSED, WS><<<1, 32, 0, ctx.st>>>(u, ctx.g.n2, ctx.h->bc, ctx.h->c, w);
         g_launches++;
         if (cudaGetLastError() != cudaSuccess) return STENCIL_ECUDA;
     }
     return STENCIL_OK;
+}
+
+template <int R>
+static int gs_1d(const RunCtx& ctx, double* u, int64_t T)
+{
+    if (ctx.sd.field) return gs_1d<R>(ctx, u, T, WField<2 * R + 1>{ctx.sd.field, ctx.sd.npts});
+    WArr<2 * R + 1> w;
+    for (int q = 0; q < 2 * R + 1; ++q) w.w[q] = ctx.h->w_desc[q];
+    return gs_1d<R>(ctx, u, T, w);
 }
 
 int gs_plain_run(const RunCtx& ctx, double* u, int64_t T)

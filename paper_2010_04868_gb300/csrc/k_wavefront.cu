@@ -105,8 +105,8 @@ __device__ __noinline__ int64_t wait_progress(const unsigned long long* p, int64
 // step is already the newest one it needs at the NEXT step, so the partial sum
 // over the previous-sweep terms (+R .. 0) is formed one step ahead, and only
 // the R newest-value terms (-1 .. -R) remain on the step-to-step chain.
-template <int R, int ARITH>
-__global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_t n, double c, WArr<2 * R + 1> w,
+template <int R, int ARITH, class WS>
+__global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_t n, double c, WS w,
                                                   int64_t T, unsigned long long* progress, int* ticket, int* status,
                                                   unsigned tag, WaitCfg wc)
 {
@@ -151,18 +151,28 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
     }
 #pragma unroll
     for (int a = 0; a < R; ++a) nw[a] = c;
-    // descending canonical order: +R .. +1, 0 (previous sweep), then -1 .. -R (this sweep)
-    auto partial = [&]() -> double {
-        double acc = __dmul_rn(w.w[0], ring[R]);
+    // Weights of point xx (clamped into the grid: a lane outside it computes a
+    // value nobody stores). wcur: point x of this step; wnext: point x + 1,
+    // loaded a step ahead so that per-point weights add no load latency to
+    // the step. Constant weights fold to immediates.
+    auto wat = [&](int q, int64_t xx) -> double { return w.at(q, xx < 0 ? 0 : (xx >= n ? n - 1 : xx)); };
+    double wcur[2 * R + 1], wnext[2 * R + 1];
 #pragma unroll
-        for (int q = 1; q <= R; ++q) acc = acc_step<ARITH>(acc, w.w[q], ring[R - q]);
+    for (int q = 0; q <= 2 * R; ++q) wcur[q] = wat(q, -(int64_t)S * lane);
+    // descending canonical order: +R .. +1, 0 (previous sweep), then -1 .. -R (this sweep)
+    auto partial = [&](const double* wq) -> double {
+        double acc = __dmul_rn(wq[0], ring[R]);
+#pragma unroll
+        for (int q = 1; q <= R; ++q) acc = acc_step<ARITH>(acc, wq[q], ring[R - q]);
         return acc;
     };
-    double pc = partial();
+    double pc = partial(wcur);
     double out = c;
     const int64_t steps = n + (int64_t)S * (L - 1);
     for (int64_t step = 0; step < steps; ++step) {
         const int64_t x = step - (int64_t)S * lane;
+#pragma unroll
+        for (int q = 0; q <= 2 * R; ++q) wnext[q] = wat(q, x + 1);
         const int64_t p = step + R + 1;  // newest previous-sweep position lane 0 takes in this step
         if ((p >> 5) != cur_ch) {
             cur_ch = p >> 5;
@@ -176,7 +186,7 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
         if (lane == 0) recv = p < n ? bottom : c;
         double acc = pc;
 #pragma unroll
-        for (int a = 1; a <= R; ++a) acc = acc_step<ARITH>(acc, w.w[R + a], nw[a - 1]);
+        for (int a = 1; a <= R; ++a) acc = acc_step<ARITH>(acc, wcur[R + a], nw[a - 1]);
         const bool inside = x >= 0 && x < n;
         out = inside ? acc : c;
 #pragma unroll
@@ -185,7 +195,9 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
 #pragma unroll
         for (int o = 0; o < R; ++o) ring[o] = ring[o + 1];
         ring[R] = recv;
-        pc = partial();
+        pc = partial(wnext);
+#pragma unroll
+        for (int q = 0; q <= 2 * R; ++q) wcur[q] = wnext[q];
         if (top) {
             if (inside) u[x] = acc;
             if (publish && (step & 63) == 63 && x >= 0) {
@@ -419,8 +431,8 @@ __host__ __device__ constexpr bool needed(int r0, int r1, int cc)
 // One step of one lane: W points along the fast axis starting at (p0, p1, p2).
 // The window of neighbour values is loaded first (nothing this step writes is
 // read through it except the same-row left values, which come from regs).
-template <int DIM, int SHAPE, int R, int ARITH, int W>
-__device__ __forceinline__ void lane_step(double* __restrict__ u, const Geo& g, double c, const double* w, int64_t p0,
+template <int DIM, int SHAPE, int R, int ARITH, int W, class WS>
+__device__ __forceinline__ void lane_step(double* __restrict__ u, const Geo& g, double c, const WS& w, int64_t p0,
                                           int64_t p1, int64_t p2)
 {
     using St = Stn<DIM, SHAPE, R>;
@@ -442,28 +454,29 @@ __device__ __forceinline__ void lane_step(double* __restrict__ u, const Geo& g, 
                     win[a][bq][cc] = in ? __ldcg(u + (q0 * g.n1 + q1) * g.n2 + q2) : c;
                 }
             }
+    const int64_t row = (p0 * g.n1 + p1) * g.n2;
 #pragma unroll
     for (int m = 0; m < W; ++m) {
         const int64_t q2 = p2 + m;
+        const int64_t pw = row + (q2 < 0 ? 0 : (q2 >= g.n2 ? g.n2 - 1 : q2));  // weights' point (clamped)
         double v[St::K];
 #pragma unroll
         for (int q = 0; q < St::K; ++q) {
             const int o0 = St::o(q, 0), o1 = St::o(q, 1), o2 = St::o(q, 2);
             v[q] = win[DIM == 3 ? o0 + R : 0][o1 + R][m + o2 + R];
         }
-        double acc = __dmul_rn(w[0], v[0]);
+        double acc = __dmul_rn(w.at(0, pw), v[0]);
 #pragma unroll
-        for (int q = 1; q < St::K; ++q) acc = acc_step<ARITH>(acc, w[q], v[q]);
+        for (int q = 1; q < St::K; ++q) acc = acc_step<ARITH>(acc, w.at(q, pw), v[q]);
         if (q2 >= 0 && q2 < g.n2) {
-            u[(p0 * g.n1 + p1) * g.n2 + q2] = acc;
+            u[row + q2] = acc;
             win[DIM == 3 ? R : 0][R][m + R] = acc;  // newest value, read by the next points as a left neighbour
         }
     }
 }
 
-template <int DIM, int SHAPE, int R, int ARITH, int W>
-__global__ void __launch_bounds__(128) k_gs_wave(double* __restrict__ u, Geo g, double c,
-                                                 WArr<Stn<DIM, SHAPE, R>::K> w, WaveGeo wg,
+template <int DIM, int SHAPE, int R, int ARITH, int W, class WS>
+__global__ void __launch_bounds__(128) k_gs_wave(double* __restrict__ u, Geo g, double c, WS w, WaveGeo wg,
                                                  const int64_t* __restrict__ pre, int* __restrict__ flags,
                                                  int* __restrict__ ticket, int* status, int tag, WaitCfg wc)
 {
@@ -492,27 +505,26 @@ __global__ void __launch_bounds__(128) k_gs_wave(double* __restrict__ u, Geo g, 
         const int64_t L = wg.T - 32 * b < 32 ? wg.T - 32 * b : 32;
         const bool active = ok && lane < L;
         const int nsteps = DIM == 3 ? wg.H * wg.HJ : wg.H;
+        // the points (p0, p1, p2 .. p2 + W - 1) this lane updates at step st; false if none is in the grid
+        auto coords = [&](int st, int64_t& p0, int64_t& p1, int64_t& p2) -> bool {
+            if (DIM == 2) {
+                p0 = 0;
+                p1 = I * wg.H + st - (int64_t)wg.s * lane;
+                if (p1 < 0 || p1 >= g.n1) return false;
+                p2 = J * W - (int64_t)wg.a1 * p1 - (int64_t)wg.b1 * lane;
+            } else {
+                p0 = I * wg.H + st / wg.HJ - (int64_t)wg.s * lane;
+                if (p0 < 0 || p0 >= g.n0) return false;
+                p1 = J * wg.HJ + st % wg.HJ - (int64_t)wg.a1 * p0 - (int64_t)wg.b1 * lane;
+                if (p1 < 0 || p1 >= g.n1) return false;
+                p2 = K * W - (int64_t)wg.a2 * p0 - (int64_t)wg.c2 * p1 - (int64_t)wg.b2 * lane;
+            }
+            return p2 + W > 0 && p2 < g.n2;
+        };
         for (int st = 0; st < nsteps; ++st) {
             if (active) {
-                if (DIM == 2) {
-                    const int64_t i2 = I * wg.H + st;
-                    const int64_t p1 = i2 - (int64_t)wg.s * lane;
-                    if (p1 >= 0 && p1 < g.n1) {
-                        const int64_t p2 = J * W - (int64_t)wg.a1 * p1 - (int64_t)wg.b1 * lane;
-                        if (p2 + W > 0 && p2 < g.n2) lane_step<DIM, SHAPE, R, ARITH, W>(u, g, c, w.w, 0, p1, p2);
-                    }
-                } else {
-                    const int64_t i2 = I * wg.H + st / wg.HJ;
-                    const int64_t j2 = J * wg.HJ + st % wg.HJ;
-                    const int64_t p0 = i2 - (int64_t)wg.s * lane;
-                    if (p0 >= 0 && p0 < g.n0) {
-                        const int64_t p1 = j2 - (int64_t)wg.a1 * p0 - (int64_t)wg.b1 * lane;
-                        if (p1 >= 0 && p1 < g.n1) {
-                            const int64_t p2 = K * W - (int64_t)wg.a2 * p0 - (int64_t)wg.c2 * p1 - (int64_t)wg.b2 * lane;
-                            if (p2 + W > 0 && p2 < g.n2) lane_step<DIM, SHAPE, R, ARITH, W>(u, g, c, w.w, p0, p1, p2);
-                        }
-                    }
-                }
+                int64_t p0, p1, p2;
+                if (coords(st, p0, p1, p2)) lane_step<DIM, SHAPE, R, ARITH, W>(u, g, c, w, p0, p1, p2);
             }
             __syncwarp();
         }
@@ -589,9 +601,8 @@ __global__ void k_sweepdag_prefix(SweepDag t, int64_t* pre)
     }
 }
 
-template <int DIM, int SHAPE, int R, int ARITH>
-__global__ void __launch_bounds__(256) k_gs_sweepdag(double* __restrict__ u, Geo g, int bc, double c,
-                                                     WArr<Stn<DIM, SHAPE, R>::K> w, SweepDag t,
+template <int DIM, int SHAPE, int R, int ARITH, class WS>
+__global__ void __launch_bounds__(256) k_gs_sweepdag(double* __restrict__ u, Geo g, int bc, double c, WS w, SweepDag t,
                                                      const int64_t* __restrict__ pre, int* __restrict__ flags,
                                                      unsigned long long* __restrict__ ctr, int* status, WaitCfg wc)
 {
@@ -660,8 +671,8 @@ __global__ void __launch_bounds__(256) k_gs_sweepdag(double* __restrict__ u, Geo
             const int64_t k = kb + ls;
             if (owner && k >= 0 && k < g.n2) {
                 const int64_t p = i * s0 + j * s1 + k;
-                u[p] = (in01 && k >= R && k < g.n2 - R) ? update_interior<DIM, SHAPE, R, ARITH, false>(u, p, s0, s1, w.w)
-                                                        : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w.w);
+                u[p] = (in01 && k >= R && k < g.n2 - R) ? update_interior<DIM, SHAPE, R, ARITH, false>(u, p, s0, s1, w)
+                                                        : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w);
             }
             __syncthreads();
         }
@@ -717,6 +728,20 @@ static WaitCfg take_wait_cfg(stencil_handle_s* h)
     return wc;
 }
 
+template <int R, class WS>
+static void launch_gs1d_wave(const RunCtx& ctx, double* u, int64_t T, const WS& w, unsigned long long* progress,
+                             int* ticket, unsigned tag, const WaitCfg& wc)
+{
+    const stencil_handle_s* h = ctx.h;
+    const unsigned nB = (unsigned)((T + 31) / 32);
+    if (h->arith == ARITH_FMA)
+        k_gs1d_wave<R, ARITH_FMA, WS><<<nB, 32, 0, ctx.st>>>(u, ctx.g.n2, h->c, w, T, progress, ticket, h->d_status,
+                                                             tag, wc);
+    else
+        k_gs1d_wave<R, ARITH_UNFUSED, WS><<<nB, 32, 0, ctx.st>>>(u, ctx.g.n2, h->c, w, T, progress, ticket,
+                                                                 h->d_status, tag, wc);
+}
+
 template <int R>
 static int wave_1d(const RunCtx& ctx, double* u, int64_t T, bool prepare_only = false)
 {
@@ -733,7 +758,9 @@ static int wave_1d(const RunCtx& ctx, double* u, int64_t T, bool prepare_only = 
     const unsigned tag = 1;
     if (cudaMemsetAsync(h->wave_ws, 0, bytes, ctx.st) != cudaSuccess) return STENCIL_ECUDA;
     const WaitCfg wc = take_wait_cfg(h);
-    if (R == 1) {
+    if (ctx.sd.field) {  // per-point weights: the single-warp kernel
+        launch_gs1d_wave<R>(ctx, u, T, WField<2 * R + 1>{ctx.sd.field, ctx.sd.npts}, progress, ticket, tag, wc);
+    } else if (R == 1) {
         WArr<3> w3;
         for (int q = 0; q < 3; ++q) w3.w[q] = w.w[q];
         if (h->arith == ARITH_FMA)
@@ -742,25 +769,25 @@ static int wave_1d(const RunCtx& ctx, double* u, int64_t T, bool prepare_only = 
         else
             k_gs1d_wave3<ARITH_UNFUSED><<<(unsigned)nB, 96, 0, ctx.st>>>(u, ctx.g.n2, h->c, w3, T, progress, ticket,
                                                                           h->d_status, tag, wc);
-    } else if (h->arith == ARITH_FMA) {
-        k_gs1d_wave<R, ARITH_FMA><<<(unsigned)nB, 32, 0, ctx.st>>>(u, ctx.g.n2, h->c, w, T, progress, ticket,
-                                                                     h->d_status, tag, wc);
     } else {
-        k_gs1d_wave<R, ARITH_UNFUSED><<<(unsigned)nB, 32, 0, ctx.st>>>(u, ctx.g.n2, h->c, w, T, progress, ticket,
-                                                                         h->d_status, tag, wc);
+        launch_gs1d_wave<R>(ctx, u, T, w, progress, ticket, tag, wc);
     }
     g_launches++;
     return cuda_rc(cudaGetLastError());
 }
+
+template <int DIM, int SHAPE, int R, int W, class WS>
+static int launch_wave(const RunCtx& ctx, double* u, const WS& w, const WaveGeo& wg, const int64_t* dpre, int* flags,
+                       int* ticket, int tag);
+template <int DIM, int SHAPE, int R, class WS>
+static int launch_sweepdag(const RunCtx& ctx, double* u, const WS& w, const SweepDag& t, const int64_t* dpre,
+                           int* flags, unsigned long long* ctr);
 
 template <int DIM, int SHAPE, int R, int W>
 static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes, bool prepare_only = false)
 {
     (void)lanes;
     stencil_handle_s* h = ctx.h;
-    constexpr int K = Stn<DIM, SHAPE, R>::K;
-    WArr<K> w;
-    for (int q = 0; q < K; ++q) w.w[q] = h->w_desc[q];
     const Geo& g = ctx.g;
     const bool box = SHAPE == BOX;
     WaveGeo wg;
@@ -823,7 +850,21 @@ static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes, bool p
     if (cudaMemsetAsync(flags, 0, (size_t)wg.ntiles * sizeof(int), ctx.st) != cudaSuccess) return STENCIL_ECUDA;
     k_wave_prefix<DIM><<<1, 256, 0, ctx.st>>>(wg, dpre);
     g_launches++;
-    auto kern = h->arith == ARITH_FMA ? k_gs_wave<DIM, SHAPE, R, ARITH_FMA, W> : k_gs_wave<DIM, SHAPE, R, ARITH_UNFUSED, W>;
+    constexpr int K = Stn<DIM, SHAPE, R>::K;
+    if (ctx.sd.field)
+        return launch_wave<DIM, SHAPE, R, W>(ctx, u, WField<K>{ctx.sd.field, ctx.sd.npts}, wg, dpre, flags, ticket, tag);
+    WArr<K> w;
+    for (int q = 0; q < K; ++q) w.w[q] = h->w_desc[q];
+    return launch_wave<DIM, SHAPE, R, W>(ctx, u, w, wg, dpre, flags, ticket, tag);
+}
+
+template <int DIM, int SHAPE, int R, int W, class WS>
+static int launch_wave(const RunCtx& ctx, double* u, const WS& w, const WaveGeo& wg, const int64_t* dpre, int* flags,
+                       int* ticket, int tag)
+{
+    stencil_handle_s* h = ctx.h;
+    auto kern = h->arith == ARITH_FMA ? k_gs_wave<DIM, SHAPE, R, ARITH_FMA, W, WS>
+                                      : k_gs_wave<DIM, SHAPE, R, ARITH_UNFUSED, W, WS>;
     int nsm = 0, per_sm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -834,7 +875,7 @@ static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes, bool p
     const int64_t need = (wg.ntiles + 3) / 4;
     if (nblk > need) nblk = need;
     const WaitCfg wc = take_wait_cfg(h);
-    kern<<<(unsigned)nblk, 128, 0, ctx.st>>>(u, g, h->c, w, wg, dpre, flags, ticket, h->d_status, tag, wc);
+    kern<<<(unsigned)nblk, 128, 0, ctx.st>>>(u, ctx.g, h->c, w, wg, dpre, flags, ticket, h->d_status, tag, wc);
     g_launches++;
     return cuda_rc(cudaGetLastError());
 }
@@ -843,9 +884,6 @@ template <int DIM, int SHAPE, int R>
 static int sweep_dag(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
 {
     stencil_handle_s* h = ctx.h;
-    constexpr int K = Stn<DIM, SHAPE, R>::K;
-    WArr<K> w;
-    for (int q = 0; q < K; ++q) w.w[q] = h->w_desc[q];
     const Geo& g = ctx.g;
     const bool box = SHAPE == BOX;
     SweepDag t;
@@ -878,7 +916,22 @@ static int sweep_dag(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
     if (cudaMemsetAsync(flags, 0, (size_t)t.sweep_units * sizeof(int), ctx.st) != cudaSuccess) return STENCIL_ECUDA;
     k_sweepdag_prefix<<<1, 256, 0, ctx.st>>>(t, dpre);
     g_launches++;
-    auto kern = h->arith == ARITH_FMA ? k_gs_sweepdag<DIM, SHAPE, R, ARITH_FMA> : k_gs_sweepdag<DIM, SHAPE, R, ARITH_UNFUSED>;
+    constexpr int K = Stn<DIM, SHAPE, R>::K;
+    if (ctx.sd.field)
+        return launch_sweepdag<DIM, SHAPE, R>(ctx, u, WField<K>{ctx.sd.field, ctx.sd.npts}, t, dpre, flags, ctr);
+    WArr<K> w;
+    for (int q = 0; q < K; ++q) w.w[q] = h->w_desc[q];
+    return launch_sweepdag<DIM, SHAPE, R>(ctx, u, w, t, dpre, flags, ctr);
+}
+
+template <int DIM, int SHAPE, int R, class WS>
+static int launch_sweepdag(const RunCtx& ctx, double* u, const WS& w, const SweepDag& t, const int64_t* dpre,
+                           int* flags, unsigned long long* ctr)
+{
+    stencil_handle_s* h = ctx.h;
+    const int64_t T = t.T;
+    auto kern = h->arith == ARITH_FMA ? k_gs_sweepdag<DIM, SHAPE, R, ARITH_FMA, WS>
+                                      : k_gs_sweepdag<DIM, SHAPE, R, ARITH_UNFUSED, WS>;
     int nsm = 0, per_sm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -887,7 +940,7 @@ static int sweep_dag(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
     int64_t nblk = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
     if (nblk > t.sweep_units * T) nblk = t.sweep_units * T;
     const WaitCfg wc = take_wait_cfg(h);
-    kern<<<(unsigned)nblk, nthr, 0, ctx.st>>>(u, g, h->bc, h->c, w, t, dpre, flags, ctr, h->d_status, wc);
+    kern<<<(unsigned)nblk, nthr, 0, ctx.st>>>(u, ctx.g, h->bc, h->c, w, t, dpre, flags, ctr, h->d_status, wc);
     g_launches++;
     return cuda_rc(cudaGetLastError());
 }
@@ -935,7 +988,7 @@ int gs_wavefront_prepare(stencil_handle_s* h, const Geo& g, int64_t T)
     ctx.h = h;
     ctx.g = g;
     ctx.st = 0;
-    ctx.sd = StencilDev{h->K, h->r, h->bc, h->arith, h->c, h->d_w, h->d_off, h->d_status};
+    ctx.sd = make_sd(h, g.n0 * g.n1 * g.n2);
     return wave_dispatch(ctx, nullptr, T, 0, true);
 }
 

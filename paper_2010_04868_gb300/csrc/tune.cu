@@ -45,8 +45,8 @@ std::string plan_key(const stencil_handle_s* h, const Geo& g, int64_t T)
 {
     char buf[160];
     const int tcls = T < 8 ? 0 : (T < 64 ? 1 : (T < 512 ? 2 : 3));
-    snprintf(buf, sizeof buf, "d%d_s%d_r%d_m%d_b%d_a%d_e%d.%d.%d_t%d", h->dim, h->shape, h->r, h->method, h->bc,
-             h->arith, log2_bucket(g.n0), log2_bucket(g.n1), log2_bucket(g.n2), tcls);
+    snprintf(buf, sizeof buf, "d%d_s%d_r%d_m%d_b%d_a%d_f%d_e%d.%d.%d_t%d", h->dim, h->shape, h->r, h->method, h->bc,
+             h->arith, h->field ? 1 : 0, log2_bucket(g.n0), log2_bucket(g.n1), log2_bucket(g.n2), tcls);
     return buf;
 }
 
@@ -193,6 +193,7 @@ Plan plan_for(const stencil_handle_s* hc, const Geo& g, int64_t T, cudaStream_t 
         return default_plan(h, g);
     }
     if (getenv("STENCIL_NO_TUNE")) return default_plan(h, g);
+    if (!jacobi_blocked_supported(h, g)) return default_plan(h, g);  // the plain kernel is the only candidate
     const size_t n = (size_t)(g.n0 * g.n1 * g.n2);
     double *a = nullptr, *b = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {

@@ -74,3 +74,20 @@ def normalized_weights(seed: int, k: int) -> np.ndarray:
     for v in r:
         s = s + float(v)
     return np.array([float(v) / s for v in r], dtype=np.float64)
+
+
+def normalized_field(seed: int, k: int, ext) -> np.ndarray:
+    """Per-point weights for a variable-coefficient stencil: shape (k,) + ext, canonical term order.
+
+    At every point p, r_q(p) = 1 - U lies in (0, 1] (U drawn term-major: all
+    points of term 0, then term 1, ...) and f_q(p) = r_q(p) / (r_0(p) + ...
+    + r_{k-1}(p)), the sum taken left to right in float64: positive weights
+    summing to about 1 at each point, so repeated steps stay bounded.
+    """
+    ext = tuple(int(e) for e in ext)
+    n = int(np.prod(ext)) if ext else 0
+    r = (1.0 - uniform(seed, k * n)).reshape((k, n))
+    s = np.zeros(n)
+    for q in range(k):
+        s = s + r[q]
+    return (r / s).reshape((k,) + ext)

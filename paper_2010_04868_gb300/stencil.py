@@ -30,7 +30,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgb300ste
 #: Every entry point that include/stencil.h declares.
 EXPORTS = ("stencil_create", "stencil_set_plan", "stencil_run", "stencil_run_batch", "stencil_workspace_bytes",
            "stencil_status", "stencil_destroy", "stencil_strerror", "stencil_run_host", "stencil_launch_count",
-           "stencil_run_noalloc", "stencil_debug_inject_stall")
+           "stencil_run_noalloc", "stencil_debug_inject_stall", "stencil_set_coeff_field")
 
 #: Largest grid (points) stencil_run_noalloc accepts: its fixed workspace holds 2^21 doubles.
 NOALLOC_MAX_POINTS = 1 << 21
@@ -64,6 +64,7 @@ def load(path: str = LIB_PATH):
     lib.stencil_run_host.argtypes = [P, P, ctypes.POINTER(I64), P, P, I64, P]
     lib.stencil_run_noalloc.argtypes = [P, ctypes.POINTER(stencil_grid), I64, P]
     lib.stencil_debug_inject_stall.argtypes = [P, I64, I]
+    lib.stencil_set_coeff_field.argtypes = [P, P, ctypes.POINTER(I64)]
     lib.stencil_launch_count.argtypes = []
     lib.stencil_launch_count.restype = ctypes.c_uint64
     for name in EXPORTS:
@@ -120,6 +121,12 @@ def stencil_run_batch(handles, grids, Ts, stream_ptr=None):
     G = (stencil_grid * n)(*grids)
     T = (ctypes.c_int64 * n)(*[int(t) for t in Ts])
     return check(load().stencil_run_batch(H, G, T, n, stream_ptr), "stencil_run_batch")
+
+
+def stencil_set_coeff_field(h, field_ptr, ext):
+    """Bind per-point weights (device pointer to K x N doubles, canonical term-major); None unbinds."""
+    e = (ctypes.c_int64 * 3)(*(list(ext) + [1] * (3 - len(ext))))
+    return check(load().stencil_set_coeff_field(h, field_ptr, e), "stencil_set_coeff_field")
 
 
 def stencil_workspace_bytes(h, grid: stencil_grid) -> int:
@@ -193,6 +200,20 @@ class Stencil:
 
     def set_plan(self, kernel, tb=0, tile=(0, 0, 0)):
         stencil_set_plan(self.handle, kernel, tb, tile)
+        return self
+
+    def set_field(self, field):
+        """Bind per-point weights: a float64 CUDA tensor of shape (K,) + grid shape, canonical term order
+        (None unbinds). The handle keeps a reference so the memory outlives the binding."""
+        if field is None:
+            stencil_set_coeff_field(self.handle, None, (0, 0, 0))
+            self._field = None
+            return self
+        _check_tensor(field, "field")
+        if field.dim() != self.dim + 1:
+            raise ValueError("field must have shape (K,) + grid shape")
+        stencil_set_coeff_field(self.handle, field.data_ptr(), tuple(field.shape[1:]))
+        self._field = field
         return self
 
     def grid(self, u, scratch=None):

@@ -23,6 +23,11 @@ Configurations (name: stencil, grid, T, boundary):
   jacobi2d9s  Jacobi 2D 9-point star (radius 2), 4096^2, T = 200, zero halo
   jacobi3d13  Jacobi 3D 13-point star (radius 2), 256^3, T = 100, zero halo
   gs2d9s      Gauss-Seidel 2D 9-point star (radius 2), 4096^2, T = 100, zero halo
+  jacobi2d5v  Jacobi 2D 5-point, per-point weights (a coefficient field), 4096^2, T = 200, zero halo
+  gs2d5v      Gauss-Seidel 2D 5-point, per-point weights, 4096^2, T = 200, zero halo
+  gs1d3v      Gauss-Seidel 1D 3-point, per-point weights, N = 2^24, T = 200, zero halo
+  jacobi3d7v  Jacobi 3D 7-point, per-point weights, 256^3, T = 100, periodic
+              (fields: inputs.normalized_field, positive and summing to about 1 at each point)
   batch3d     jacobi3d7 + jacobi3d27 + gs3d7 in one stencil_run_batch call (one persistent launch
               replayed from a CUDA graph), against the same three run one after another
 """
@@ -52,7 +57,14 @@ CONFIGS = {
     "jacobi2d9s": (2, 0, 0, (4096, 4096), 200, 0, 309),
     "jacobi3d13": (3, 0, 0, (256, 256, 256), 100, 0, 313),
     "gs2d9s": (2, 0, 1, (4096, 4096), 100, 0, 319),
+    # variable coefficients (the weights come from a per-point field; the seed offset seeds the field)
+    "jacobi2d5v": (2, 0, 0, (4096, 4096), 200, 0, 405),
+    "gs2d5v": (2, 0, 1, (4096, 4096), 200, 0, 415),
+    "gs1d3v": (1, 0, 1, (1 << 24,), 200, 0, 403),
+    "jacobi3d7v": (3, 0, 0, (256, 256, 256), 100, 1, 407),
 }
+
+FIELD = {"jacobi2d5v", "gs2d5v", "gs1d3v", "jacobi3d7v"}
 
 RADIUS = {"jacobi1d5": 2, "jacobi2d9s": 2, "jacobi3d13": 2, "gs2d9s": 2}
 
@@ -70,6 +82,11 @@ def config_weights(name):
     return list(inputs.normalized_weights(inputs.SEED_BASE + w, k_points(dim, shape, RADIUS.get(name, 1))))
 
 
+def config_field(name):
+    dim, shape, _, ext, _, _, seed = CONFIGS[name]
+    return inputs.normalized_field(inputs.SEED_BASE + seed, k_points(dim, shape, RADIUS.get(name, 1)), ext)
+
+
 def config_grid(name):
     ext = CONFIGS[name][3]
     return inputs.grid(inputs.SEED_BASE + 10 + list(CONFIGS).index(name), ext)
@@ -84,6 +101,8 @@ def run(name, kernel="auto", T=None, reps=2, tb=0, tile=(0, 0, 0), sm_mhz=2070.0
     T = T0 if T is None else T
     u0 = torch.from_numpy(config_grid(name)).cuda()
     st = S.Stencil(dim, shape, r, config_weights(name), method, bc)
+    if name in FIELD:
+        st.set_field(torch.from_numpy(config_field(name)).cuda())
     if kernel != "auto":
         st.set_plan(KERNELS[kernel], tb, tile)
     u = u0.clone()
@@ -114,9 +133,11 @@ def run(name, kernel="auto", T=None, reps=2, tb=0, tile=(0, 0, 0), sm_mhz=2070.0
     gst = npts * T / ms / 1e6
     k = k_points(dim, shape, r)
     peak = FP64_OPS_PER_SM_CLK * N_SM * sm_mhz / 1e3
+    # one pass per step moves the grid in and out, plus the K field planes with per-point weights
+    bytes_pt = 16 + (8 * k if name in FIELD else 0)
     return {"config": name, "kernel": kernel, "r": r, "T": T, "ms": round(ms, 3), "gstencil_s": round(gst, 3),
             "launches": launches, "fp64_gops": round(gst * k, 1), "fp64_frac_of_peak": round(gst * k / peak, 4),
-            "hbm_gbs_one_pass_per_step": round(gst * 16, 1)}
+            "hbm_gbs_one_pass_per_step": round(gst * bytes_pt, 1)}
 
 
 def run_batch3d(reps=2):
