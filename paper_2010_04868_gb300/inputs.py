@@ -91,3 +91,10 @@ def normalized_field(seed: int, k: int, ext) -> np.ndarray:
     for q in range(k):
         s = s + r[q]
     return (r / s).reshape((k,) + ext)
+
+
+def cells(seed: int, ext, density: float = 0.5) -> np.ndarray:
+    """A 0/1 uint8 grid: cell = 1 where U < density (U uniform [0, 1), SplitMix64 in C order)."""
+    ext = tuple(int(e) for e in ext)
+    n = int(np.prod(ext)) if ext else 0
+    return (uniform(seed, n) < density).astype(np.uint8).reshape(ext)
