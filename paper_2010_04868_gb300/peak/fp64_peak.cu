@@ -1,4 +1,6 @@
 // FP64 pipe micro-benchmark: the ALU roofline the stencil kernels are measured against.
+// Also the 32-bit integer logic (LOP3) and funnel-shift (SHF) rates, the roofline of the
+// bit-packed Game of Life kernels.
 //
 // Streams of independent __fma_rn / __dadd_rn / __dmul_rn on every resident
 // warp, timed with clock64() per CTA (SM clocks, so the result is a per-clock
@@ -35,6 +37,34 @@ __global__ void stream_ops(double* out, long long* cyc, int iters, double a, dou
 #pragma unroll
     for (int c = 0; c < CH; ++c) s += x[c];
     if (s == 12345.678) out[0] = s;
+    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+}
+
+// Independent chains of one 3-input logic op (LOP3) or one funnel shift (SHF) per step, written
+// in PTX so that the compiler cannot fold the repeated bitwise operations.
+template <int CH, int OP>
+__global__ void stream_int(double* out, long long* cyc, int iters, double fa, double fb, int active)
+{
+    if ((int)(threadIdx.x & 31) >= active) return;
+    const unsigned a = (unsigned)(fa * 1e7) | 1u, b = (unsigned)(fb * 1e9) + 3u;
+    unsigned x[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) x[c] = threadIdx.x * 7u + c;
+    const long long t0 = clock64();
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            if (OP == 0)
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x[c]) : "r"(a), "r"(b));
+            else
+                asm volatile("shf.l.wrap.b32 %0, %0, %1, 1;" : "+r"(x[c]) : "r"(b));
+        }
+    }
+    const long long t1 = clock64();
+    unsigned s = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) s ^= x[c];
+    if (s == 0x12345678u) out[0] = s;
     if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
 }
 
@@ -79,14 +109,18 @@ int main()
     const double mul_clk = rate(stream_ops<8, 2>, 128, 4096, 8, 32, s_mul);
     const double one_lane_clk = rate(stream_ops<8, 0>, 128, 4096, 8, 1, s_one);
     const double chain_clk = rate(stream_ops<1, 0>, 32, 4096, 1, 1, s_lat);  // 1 lane, dependent chain
+    double s_lop, s_shf;
+    const double lop_clk = rate(stream_int<8, 0>, 512, 4096, 8, 32, s_lop);  // 16 warps: the integer pipes are wider
+    const double shf_clk = rate(stream_int<8, 1>, 512, 4096, 8, 32, s_shf);
     int clk_khz = 0;
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, 0);
     printf("{\"device\": \"%s\", \"sms\": %d, \"max_sm_mhz\": %.0f, "
            "\"fp64_fma_lane_ops_per_sm_clk\": %.4f, \"fp64_add_lane_ops_per_sm_clk\": %.4f, "
            "\"fp64_mul_lane_ops_per_sm_clk\": %.4f, \"fp64_fma_gops_measured\": %.1f, "
            "\"fp64_fma_gops_at_max_clock\": %.1f, \"one_active_lane_lane_ops_per_sm_clk\": %.4f, "
-           "\"dependent_dfma_latency_clk\": %.1f}\n",
+           "\"dependent_dfma_latency_clk\": %.1f, \"int_lop3_lane_ops_per_sm_clk\": %.2f, "
+           "\"int_shf_lane_ops_per_sm_clk\": %.2f, \"int_lop3_gops_measured\": %.1f}\n",
            p.name, nsm, clk_khz / 1e3, fma_clk, add_clk, mul_clk, s_fma / 1e9, fma_clk * nsm * clk_khz / 1e6,
-           one_lane_clk, 1.0 / chain_clk);
+           one_lane_clk, 1.0 / chain_clk, lop_clk, shf_clk, s_lop / 1e9);
     return 0;
 }

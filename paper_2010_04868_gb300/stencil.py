@@ -30,7 +30,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgb300ste
 #: Every entry point that include/stencil.h declares.
 EXPORTS = ("stencil_create", "stencil_set_plan", "stencil_run", "stencil_run_batch", "stencil_workspace_bytes",
            "stencil_status", "stencil_destroy", "stencil_strerror", "stencil_run_host", "stencil_launch_count",
-           "stencil_run_noalloc", "stencil_debug_inject_stall", "stencil_set_coeff_field")
+           "stencil_run_noalloc", "stencil_debug_inject_stall", "stencil_set_coeff_field",
+           "life_workspace_bytes", "life_run")
 
 #: Largest grid (points) stencil_run_noalloc accepts: its fixed workspace holds 2^21 doubles.
 NOALLOC_MAX_POINTS = 1 << 21
@@ -65,6 +66,8 @@ def load(path: str = LIB_PATH):
     lib.stencil_run_noalloc.argtypes = [P, ctypes.POINTER(stencil_grid), I64, P]
     lib.stencil_debug_inject_stall.argtypes = [P, I64, I]
     lib.stencil_set_coeff_field.argtypes = [P, P, ctypes.POINTER(I64)]
+    lib.life_workspace_bytes.argtypes = [ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_size_t)]
+    lib.life_run.argtypes = [P, ctypes.POINTER(I64), I, ctypes.c_uint32, ctypes.c_uint32, I64, I, P, P]
     lib.stencil_launch_count.argtypes = []
     lib.stencil_launch_count.restype = ctypes.c_uint64
     for name in EXPORTS:

@@ -30,6 +30,8 @@ Configurations (name: stencil, grid, T, boundary):
               (fields: inputs.normalized_field, positive and summing to about 1 at each point)
   batch3d     jacobi3d7 + jacobi3d27 + gs3d7 in one stencil_run_batch call (one persistent launch
               replayed from a CUDA graph), against the same three run one after another
+  life        Game of Life B2S23 (Section 3.4), 8000^2 cells, T = 2000 (the paper's Table 1 size),
+              dead boundary, seeded cells of density 1/2; --tb sets the steps per launch
 """
 from __future__ import annotations
 
@@ -140,6 +142,43 @@ def run(name, kernel="auto", T=None, reps=2, tb=0, tile=(0, 0, 0), sm_mhz=2070.0
             "hbm_gbs_one_pass_per_step": round(gst * bytes_pt, 1)}
 
 
+# Integer operations per 32-cell word and step of the bit-sliced Life update, the unit of its ALU
+# roofline: 4 full adders (2 three-input logic ops each) + 3 half adders (2 each) + the B2S23 rule (2)
+# = 16 logic ops, plus the west and east alignment of the new row (one funnel shift each).
+LIFE_OPS_PER_WORD = 18
+
+
+def run_life(T=2000, tb=0, reps=2, ext=(8000, 8000)):
+    import torch
+
+    from . import life
+    c0 = torch.from_numpy(inputs.cells(inputs.SEED_BASE + 500, ext, 0.5)).cuda()
+    c = c0.clone()
+    ws = torch.empty(life.life_workspace_bytes(ext), dtype=torch.uint8, device="cuda")
+    life.run(c, T, tb=tb, workspace=ws)
+    torch.cuda.synchronize()
+    best = None
+    from . import stencil as S
+    for _ in range(reps):
+        c.copy_(c0)
+        n0 = S.stencil_launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        life.run(c, T, tb=tb, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if best is None or ms < best[0]:
+            best = (ms, S.stencil_launch_count() - n0)
+    ms, launches = best
+    cells = ext[0] * ext[1]
+    words = ext[0] * ((ext[1] + 31) // 32)
+    return {"config": "life", "tb": tb, "T": T, "ms": round(ms, 3), "gcell_updates_s": round(cells * T / ms / 1e6, 1),
+            "launches": launches, "int_gops": round(words * T * LIFE_OPS_PER_WORD / ms / 1e6, 1),
+            "live_fraction_after": round(float(c.float().mean()), 4)}
+
+
 def run_batch3d(reps=2):
     """The three 512^3 periodic problems batched, and the same three run separately."""
     import ctypes
@@ -197,11 +236,13 @@ def main():
     ap.add_argument("--tb", type=int, default=0)
     ap.add_argument("--tile", default="0,0,0")
     a = ap.parse_args()
-    names = list(CONFIGS) + ["batch3d"] if a.config == "all" else a.config.split(",")
+    names = list(CONFIGS) + ["batch3d", "life"] if a.config == "all" else a.config.split(",")
     tile = tuple(int(x) for x in a.tile.split(","))
     for n in names:
         if n == "batch3d":
             print(json.dumps(run_batch3d(a.reps)), flush=True)
+        elif n == "life":
+            print(json.dumps(run_life(a.T or 2000, a.tb, a.reps)), flush=True)
         else:
             print(json.dumps(run(n, a.kernel, a.T, a.reps, a.tb, tile)), flush=True)
 

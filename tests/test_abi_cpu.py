@@ -13,7 +13,8 @@ def _declared():
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"\b(stencil_[a-z_]+)\s*\(", src))
+            # a declaration: a line that starts with its return type and names a function
+            names |= set(re.findall(r"^[A-Za-z_][\w \t\*]*?\b([a-z][a-z0-9_]*)\s*\(", src, flags=re.M))
     return names
 
 
