@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256) k_life_step(const uint32_t* __restrict__ 
 
 // ---------------------------------------------------- temporally blocked ---
 
-constexpr int LIFE_TILE_ROWS = 64;  // interior rows per tile
+constexpr int LIFE_TILE_ROWS = 64;  // largest interior rows per tile
 constexpr int LIFE_MAX_COLS = 128;  // tile columns (interior words + 2 halo words)
 
 struct LifeTile {
@@ -200,13 +200,11 @@ __global__ void __launch_bounds__(LIFE_THREADS) k_life_blocked(const uint32_t* _
     const int64_t gw = gw0 + col;
     const bool wvalid = g.bc == BC_PERIODIC || (gw >= 0 && gw < g.W);
     const uint32_t keep = !wvalid ? 0u : (g.bc == BC_CONSTANT && gw == g.W - 1 ? g.last_mask : FULLMASK);
-    const size_t plane = (size_t)t.rows * t.stride;
+    const int plane = t.rows * t.stride;
     for (int64_t ti = blockIdx.y; ti < ntr; ti += gridDim.y) {
-        uint32_t* s0 = smem;
-        uint32_t* s1 = smem + plane;
         const int64_t gi0 = ti * t.tr - t.tb;  // grid row of tile row 0
-        // stage the tile and its halo; out-of-grid rows and words are dead (constant) or wrapped
-        // (periodic); the guard words of both buffers are zero
+        // stage the tile and its halo into buffer 0; out-of-grid rows and words are dead (constant)
+        // or wrapped (periodic); the guard words of both buffers are zero
         for (int q = threadIdx.x; q < t.rows * t.stride; q += nthr) {
             const int r = q / t.stride, sc = q - (q / t.stride) * t.stride;
             uint32_t v = 0;
@@ -220,44 +218,51 @@ __global__ void __launch_bounds__(LIFE_THREADS) k_life_blocked(const uint32_t* _
                     v = __ldg(a + i * g.W + w);
                 }
             } else {
-                s1[q] = 0;
+                smem[plane + q] = 0;
             }
-            s0[q] = v;
+            smem[q] = v;
+        }
+        // tile rows inside the grid (the others stay dead under the constant boundary)
+        int rlo = 0, rhi = t.rows;
+        if (g.bc == BC_CONSTANT) {
+            rlo = gi0 < 0 ? (int)(-gi0) : 0;
+            rhi = g.n0 - gi0 < t.rows ? (int)(g.n0 - gi0) : t.rows;
         }
         __syncthreads();
+        // 32-bit offsets into the shared array keep every access a plain shared-memory load/store
+        int src = 0, dst = plane;
         for (int s = 1; s <= t.tb; ++s) {
             const int lo = s, hi = t.rows - s;  // rows valid after step s: [lo, hi)
             const int per = (hi - lo + t.groups - 1) / t.groups;
             const int r0 = lo + grp * per;
             const int r1 = r0 + per < hi ? r0 + per : hi;
             if (worker && r0 < r1) {
-                const uint32_t* src = s0 + col + 1;
-                uint32_t* dst = s1 + col + 1;
-                const uint32_t* p = src + (size_t)(r0 - 1) * t.stride;
-                uint32_t aw = west_of(p[-1], p[0]), ac = p[0], ae = east_of(p[0], p[1]);
-                p += t.stride;
-                uint32_t mw = west_of(p[-1], p[0]), mc = p[0], me = east_of(p[0], p[1]);
-                int64_t gi = gi0 + r0;
-                for (int r = r0; r < r1; ++r, ++gi) {
-                    p += t.stride;
-                    const uint32_t bw = west_of(p[-1], p[0]), bcv = p[0], be = east_of(p[0], p[1]);
-                    const bool rvalid = g.bc == BC_PERIODIC || (gi >= 0 && gi < g.n0);
+                int o = src + (r0 - 1) * t.stride + col + 1;
+                uint32_t aw = west_of(smem[o - 1], smem[o]), ac = smem[o], ae = east_of(smem[o], smem[o + 1]);
+                o += t.stride;
+                uint32_t mw = west_of(smem[o - 1], smem[o]), mc = smem[o], me = east_of(smem[o], smem[o + 1]);
+                int od = dst + r0 * t.stride + col + 1;
+#pragma unroll 2
+                for (int r = r0; r < r1; ++r) {
+                    o += t.stride;
+                    const uint32_t bw = west_of(smem[o - 1], smem[o]), bcv = smem[o], be = east_of(smem[o], smem[o + 1]);
                     const uint32_t nv = life_word<RULE>(aw, ac, ae, mw, me, mc, bw, bcv, be, birth, survive);
-                    dst[(size_t)r * t.stride] = rvalid ? (nv & keep) : 0u;
+                    smem[od] = (r >= rlo && r < rhi) ? (nv & keep) : 0u;
+                    od += t.stride;
                     aw = mw; ac = mc; ae = me;
                     mw = bw; mc = bcv; me = be;
                 }
             }
             __syncthreads();
-            uint32_t* tmp = s0;
-            s0 = s1;
-            s1 = tmp;
+            const int tmp = src;
+            src = dst;
+            dst = tmp;
         }
         // write the interior
         for (int q = threadIdx.x; q < t.tr * t.tw; q += nthr) {
             const int r = q / t.tw, cc = q - (q / t.tw) * t.tw;
             const int64_t i = ti * t.tr + r, w = tj * t.tw + cc;
-            if (i < g.n0 && w < g.W) b[i * g.W + w] = s0[(size_t)(r + t.tb) * t.stride + cc + 2];
+            if (i < g.n0 && w < g.W) b[i * g.W + w] = smem[src + (r + t.tb) * t.stride + cc + 2];
         }
         __syncthreads();  // the next tile's staging overwrites the buffers
     }
@@ -286,8 +291,9 @@ int rule_kind(uint32_t birth, uint32_t survive)
     return RULE_ANY;
 }
 
-// Tile shape: as few tile columns as fit LIFE_MAX_COLS, the words split evenly among them.
-LifeTile make_tile(const LifeGeo& g, int tb)
+// Tile shape: as few tile columns as fit LIFE_MAX_COLS, the words split evenly among them; tr
+// interior rows.
+LifeTile make_tile(const LifeGeo& g, int tb, int tr)
 {
     LifeTile t;
     t.tb = tb;
@@ -295,7 +301,7 @@ LifeTile make_tile(const LifeGeo& g, int tb)
     t.tw = (int)((g.W + nt - 1) / nt);
     t.cols = t.tw + 2;
     t.stride = t.cols + 2;
-    t.tr = LIFE_TILE_ROWS;
+    t.tr = tr;
     t.rows = t.tr + 2 * tb;
     t.groups = LIFE_THREADS / t.cols;
     return t;
@@ -308,12 +314,29 @@ int life_steps(const LifeGeo& g, uint32_t*& a, uint32_t*& b, int64_t T, int tb, 
     const bool blocked_ok = g.bc == BC_CONSTANT || g.m == 32;
     int64_t t = 0;
     if (tb > 1 && blocked_ok) {
-        const LifeTile tl = make_tile(g, tb > LIFE_MAX_TB ? LIFE_MAX_TB : tb);
-        const size_t smem = 2 * (size_t)tl.rows * tl.stride * sizeof(uint32_t);
+        const int tbc = tb > LIFE_MAX_TB ? LIFE_MAX_TB : tb;
+        LifeTile tl = make_tile(g, tbc, LIFE_TILE_ROWS);
+        size_t smem = 2 * (size_t)tl.rows * tl.stride * sizeof(uint32_t);
         if (smem > 227 * 1024) return STENCIL_EUNSUPPORTED;
-        if (cudaFuncSetAttribute(k_life_blocked<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(k_life_blocked<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
             cudaSuccess)
             return STENCIL_ECUDA;
+        // Tile height: the tiles of one pass fill whole waves of resident CTAs, so that no SM runs
+        // two tiles while another idles (a pass costs as much as its busiest SM).
+        int dev = 0, nsm = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_life_blocked<RULE>, LIFE_THREADS, smem);
+        const int64_t ntc = (g.W + tl.tw - 1) / tl.tw;
+        const int64_t row_tiles_per_wave = (int64_t)nsm * (per_sm > 0 ? per_sm : 1) / ntc;
+        if (row_tiles_per_wave > 0) {
+            const int64_t waves = (g.n0 + LIFE_TILE_ROWS * row_tiles_per_wave - 1) / (LIFE_TILE_ROWS * row_tiles_per_wave);
+            const int64_t tr = (g.n0 + waves * row_tiles_per_wave - 1) / (waves * row_tiles_per_wave);
+            if (tr >= 16 && tr < LIFE_TILE_ROWS) {
+                tl = make_tile(g, tbc, (int)tr);
+                smem = 2 * (size_t)tl.rows * tl.stride * sizeof(uint32_t);
+            }
+        }
         const int64_t ntr = (g.n0 + tl.tr - 1) / tl.tr;
         const dim3 grid((unsigned)((g.W + tl.tw - 1) / tl.tw), (unsigned)(ntr < 65535 ? ntr : 65535));
         for (; T - t >= tl.tb; t += tl.tb) {
