@@ -1,6 +1,7 @@
 /*
  * CPU oracle for the integer stencils: Game of Life (Section 3.4, "Game of
- * life").
+ * life") and the longest common subsequence (Section 3.4, "Longest common
+ * subsequence").
  *
  * TEST INFRASTRUCTURE ONLY. Nothing in the library's product path links,
  * loads or calls this file; only the tests, the smoke check and the
@@ -69,6 +70,34 @@ int oracle_life(int64_t n0, int64_t n1, int bc, uint32_t birth, uint32_t survive
         free(a);
     } else {
         free(b);
+    }
+    return 0;
+}
+
+/*
+ * Longest common subsequence, the dynamic-programming definition of Section
+ * 3.4: lcs[x][y] is the length of the longest common subsequence of
+ * A[1..x] and B[1..y]; lcs[0][y] = lcs[x][0] = 0 and, for x, y >= 1,
+ *     lcs[x][y] = lcs[x-1][y-1] + 1                  if A[x] == B[y]
+ *               = max(lcs[x-1][y], lcs[x][y-1])      otherwise.
+ * x (over A) is the time dimension and y (over B) the space dimension, so
+ * one row of nb + 1 values is kept and updated in place in increasing y,
+ * the 1D Gauss-Seidel form the paper gives it. On return
+ * row[y] = lcs[na][y] for y = 0..nb (row[nb] is the LCS length).
+ * Returns 0, or -1 on invalid arguments.
+ */
+int oracle_lcs(const uint8_t* A, int64_t na, const uint8_t* B, int64_t nb, int32_t* row)
+{
+    if (na < 0 || nb < 0 || !row || (na > 0 && !A) || (nb > 0 && !B)) return -1;
+    for (int64_t y = 0; y <= nb; ++y) row[y] = 0;
+    for (int64_t x = 1; x <= na; ++x) {
+        int32_t diag = 0;  /* lcs[x-1][y-1] */
+        for (int64_t y = 1; y <= nb; ++y) {
+            const int32_t up = row[y];  /* lcs[x-1][y] */
+            const int32_t left = row[y - 1];  /* lcs[x][y-1], already updated */
+            row[y] = A[x - 1] == B[y - 1] ? diag + 1 : (up > left ? up : left);
+            diag = up;
+        }
     }
     return 0;
 }

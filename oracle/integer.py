@@ -1,4 +1,4 @@
-"""CPU oracle for the integer stencils (Game of Life, Section 3.4).
+"""CPU oracle for the integer stencils (Game of Life and LCS, Section 3.4).
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 benchmark legs that time the oracle use it; the library never does. It shares
@@ -6,7 +6,9 @@ no code with the CUDA path and never imports it.
 
 ``life`` calls the plain C definition in ``int_oracle.c``: two arrays, every
 cell's 8 neighbours counted from the previous step, the birth/survival rule
-applied by table lookup in the rule's bit masks.
+applied by table lookup in the rule's bit masks. ``lcs`` calls the textbook
+dynamic program for the longest common subsequence, one row updated in
+place over B for every character of A.
 """
 from __future__ import annotations
 
@@ -42,6 +44,10 @@ def load(path: str):
     lib.oracle_life.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
                                 ctypes.c_int64, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int]
     lib.oracle_life.restype = ctypes.c_int
+    if hasattr(lib, "oracle_lcs"):
+        lib.oracle_lcs.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int64, ctypes.POINTER(ctypes.c_uint8),
+                                   ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]
+        lib.oracle_lcs.restype = ctypes.c_int
     return lib
 
 
@@ -63,3 +69,19 @@ def life(cells, T: int, *, bc: int = BC_CONSTANT, rule=B2S23, nthreads: int = 0,
     if rc != 0:
         raise ValueError("oracle_life rejected its arguments")
     return a
+
+
+def lcs(A, B, lib=None) -> np.ndarray:
+    """Row lcs[len(A)][0..len(B)] of the LCS dynamic program (int32); its last entry is the LCS length."""
+    lib = lib if lib is not None else _load()
+    a = np.ascontiguousarray(np.frombuffer(bytes(A), np.uint8) if isinstance(A, (bytes, bytearray)) else A,
+                             dtype=np.uint8)
+    b = np.ascontiguousarray(np.frombuffer(bytes(B), np.uint8) if isinstance(B, (bytes, bytearray)) else B,
+                             dtype=np.uint8)
+    row = np.zeros(len(b) + 1, np.int32)
+    P8 = ctypes.POINTER(ctypes.c_uint8)
+    rc = lib.oracle_lcs(a.ctypes.data_as(P8), len(a), b.ctypes.data_as(P8), len(b),
+                        row.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc != 0:
+        raise ValueError("oracle_lcs rejected its arguments")
+    return row

@@ -98,3 +98,8 @@ def cells(seed: int, ext, density: float = 0.5) -> np.ndarray:
     ext = tuple(int(e) for e in ext)
     n = int(np.prod(ext)) if ext else 0
     return (uniform(seed, n) < density).astype(np.uint8).reshape(ext)
+
+
+def sequence(seed: int, n: int, sigma: int = 4) -> np.ndarray:
+    """A uint8 sequence of n symbols drawn uniformly from {0, .., sigma - 1} (SplitMix64 modulo sigma)."""
+    return (splitmix64(seed, 0, int(n)) % np.uint64(sigma)).astype(np.uint8)
