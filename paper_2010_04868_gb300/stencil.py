@@ -31,7 +31,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgb300ste
 EXPORTS = ("stencil_create", "stencil_set_plan", "stencil_run", "stencil_run_batch", "stencil_workspace_bytes",
            "stencil_status", "stencil_destroy", "stencil_strerror", "stencil_run_host", "stencil_launch_count",
            "stencil_run_noalloc", "stencil_debug_inject_stall", "stencil_set_coeff_field",
-           "life_workspace_bytes", "life_run")
+           "life_workspace_bytes", "life_run", "lcs_workspace_bytes", "lcs_run", "lcs_status")
 
 #: Largest grid (points) stencil_run_noalloc accepts: its fixed workspace holds 2^21 doubles.
 NOALLOC_MAX_POINTS = 1 << 21
@@ -68,6 +68,9 @@ def load(path: str = LIB_PATH):
     lib.stencil_set_coeff_field.argtypes = [P, P, ctypes.POINTER(I64)]
     lib.life_workspace_bytes.argtypes = [ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_size_t)]
     lib.life_run.argtypes = [P, ctypes.POINTER(I64), I, ctypes.c_uint32, ctypes.c_uint32, I64, I, P, P]
+    lib.lcs_workspace_bytes.argtypes = [I64, I64, I, ctypes.POINTER(ctypes.c_size_t)]
+    lib.lcs_run.argtypes = [P, I64, P, I64, P, I, P, P]
+    lib.lcs_status.argtypes = [P, P]
     lib.stencil_launch_count.argtypes = []
     lib.stencil_launch_count.restype = ctypes.c_uint64
     for name in EXPORTS:

@@ -32,6 +32,8 @@ Configurations (name: stencil, grid, T, boundary):
               replayed from a CUDA graph), against the same three run one after another
   life        Game of Life B2S23 (Section 3.4), 8000^2 cells, T = 2000 (the paper's Table 1 size),
               dead boundary, seeded cells of density 1/2; --tb sets the steps per launch
+  lcs         LCS (Section 3.4) of two seeded sequences of 200000 symbols over 4 letters (the paper's
+              Table 1 size); --kernel dp or bits (default: both)
 """
 from __future__ import annotations
 
@@ -179,6 +181,37 @@ def run_life(T=2000, tb=0, reps=2, ext=(8000, 8000)):
             "live_fraction_after": round(float(c.float().mean()), 4)}
 
 
+def run_lcs(kernel="bits", n=200000, sigma=4, reps=2):
+    import torch
+
+    from . import lcs
+    from . import stencil as S
+    kid = {"dp": lcs.LCS_KERNEL_DP, "bits": lcs.LCS_KERNEL_BITS}[kernel]
+    A = torch.from_numpy(inputs.sequence(inputs.SEED_BASE + 700, n, sigma)).cuda()
+    B = torch.from_numpy(inputs.sequence(inputs.SEED_BASE + 701, n, sigma)).cuda()
+    ws = torch.empty(lcs.lcs_workspace_bytes(n, n, kid), dtype=torch.uint8, device="cuda")
+    row = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    lcs.run(A, B, kid, row=row, workspace=ws)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        n0 = S.stencil_launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lcs.run(A, B, kid, row=row, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if best is None or ms < best[0]:
+            best = (ms, S.stencil_launch_count() - n0)
+    if lcs.lcs_status(ws.data_ptr()) != 0:
+        raise RuntimeError("lcs: a bounded wait timed out")
+    ms, launches = best
+    return {"config": "lcs", "kernel": kernel, "n": n, "sigma": sigma, "ms": round(ms, 3),
+            "gcell_updates_s": round(n * n / ms / 1e6, 1), "launches": launches, "lcs_length": int(row[-1])}
+
+
 def run_batch3d(reps=2):
     """The three 512^3 periodic problems batched, and the same three run separately."""
     import ctypes
@@ -230,19 +263,22 @@ def run_batch3d(reps=2):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--config", default="all")
-    ap.add_argument("--kernel", default="auto", choices=list(KERNELS))
+    ap.add_argument("--kernel", default="auto", choices=list(KERNELS) + ["dp", "bits"])
     ap.add_argument("--T", type=int, default=None)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--tb", type=int, default=0)
     ap.add_argument("--tile", default="0,0,0")
     a = ap.parse_args()
-    names = list(CONFIGS) + ["batch3d", "life"] if a.config == "all" else a.config.split(",")
+    names = list(CONFIGS) + ["batch3d", "life", "lcs"] if a.config == "all" else a.config.split(",")
     tile = tuple(int(x) for x in a.tile.split(","))
     for n in names:
         if n == "batch3d":
             print(json.dumps(run_batch3d(a.reps)), flush=True)
         elif n == "life":
             print(json.dumps(run_life(a.T or 2000, a.tb, a.reps)), flush=True)
+        elif n == "lcs":
+            for k in (("dp", "bits") if a.kernel == "auto" else (a.kernel,)):
+                print(json.dumps(run_lcs(k, reps=a.reps)), flush=True)
         else:
             print(json.dumps(run(n, a.kernel, a.T, a.reps, a.tb, tile)), flush=True)
 
