@@ -74,6 +74,7 @@ extern "C" {
 #define STENCIL_KERNEL_PLAIN 1     /* one launch per Jacobi step / Gauss-Seidel sweep */
 #define STENCIL_KERNEL_BLOCKED 2   /* Jacobi: tile + halo staged in shared memory, T_b steps per pass */
 #define STENCIL_KERNEL_WAVEFRONT 3 /* Gauss-Seidel: time-skewed wavefront, warp lanes hold sweeps */
+#define STENCIL_KERNEL_DIAMOND 4   /* Jacobi: split (diamond) temporal tiles, no redundant work, in place */
 
 typedef struct stencil_handle_s* stencil_handle; /* opaque, owned by the library */
 
@@ -103,11 +104,25 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
 /*
  * Fix the kernel family and its parameters instead of the autotuned choice.
  *   kernel   STENCIL_KERNEL_* (AUTO restores the default).
- *   tb       temporal block depth T_b (BLOCKED) or sweeps per warp (WAVEFRONT,
- *            1..32); 0 = default.
- *   tile     tile extents (slowest first) for BLOCKED, 0 = default.
+ *   tb       temporal block depth T_b (BLOCKED, DIAMOND) or sweeps per warp
+ *            (WAVEFRONT, 1..32); 0 = default.
+ *   tile     tile extents (slowest first) for BLOCKED; period lengths per axis
+ *            (slowest first) for DIAMOND; 0 = default.
  * A family that cannot run a given (method, boundary, grid) makes stencil_run
  * return EUNSUPPORTED.
+ *
+ * DIAMOND (Jacobi) is the diamond temporal tiling of Section 3.4 in split
+ * form on every axis: each axis is cut into periods of an A segment (a
+ * trapezoid in space-time, shrinking by r per step) and a B segment (an
+ * inverted trapezoid, growing by r per step); the 2^dim tile types of a band
+ * of T_b steps run as 2^dim launches, A before B, and no point is computed
+ * twice. It works in place on g->data (g->scratch is not used) and keeps the
+ * per-level edge values of the tiles in a workspace owned by the handle
+ * (about 4 * T_b * r / period of the grid per axis), allocated on first use
+ * and grown when a run needs more; that first use must not be inside a
+ * stream capture (EUNSUPPORTED there). T_b is lowered to fit the shortest
+ * period (period >= 2 * T_b * r); an axis shorter than 2 * r points cannot be
+ * tiled and returns EUNSUPPORTED.
  */
 int stencil_set_plan(stencil_handle h, int kernel, int tb, const int64_t tile[3]);
 

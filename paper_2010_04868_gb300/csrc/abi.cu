@@ -119,8 +119,9 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
 
 int stencil_set_plan(stencil_handle h, int kernel, int tb, const int64_t tile[3])
 {
-    if (!h || kernel < STENCIL_KERNEL_AUTO || kernel > STENCIL_KERNEL_WAVEFRONT || tb < 0) return STENCIL_EINVAL;
-    if (kernel == STENCIL_KERNEL_BLOCKED && h->method != STENCIL_JACOBI) return STENCIL_EINVAL;
+    if (!h || kernel < STENCIL_KERNEL_AUTO || kernel > STENCIL_KERNEL_DIAMOND || tb < 0) return STENCIL_EINVAL;
+    if ((kernel == STENCIL_KERNEL_BLOCKED || kernel == STENCIL_KERNEL_DIAMOND) && h->method != STENCIL_JACOBI)
+        return STENCIL_EINVAL;
     if (kernel == STENCIL_KERNEL_WAVEFRONT && (h->method != STENCIL_GAUSS_SEIDEL || tb > 32)) return STENCIL_EINVAL;
     h->plan_kernel = kernel;
     h->plan_tb = tb;
@@ -178,6 +179,12 @@ int stencil_run(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_s
         return gs_plain_run(ctx, g->data, T);
     }
 
+    Plan p = plan_for(h, ctx.g, T, ctx.st);
+    if (p.kernel == STENCIL_KERNEL_DIAMOND) {
+        // in place: the grid's own array is the only one the split tiles need
+        if (!jacobi_diamond_supported(h, ctx.g)) return STENCIL_EUNSUPPORTED;
+        return jacobi_diamond_run(ctx, g->data, T, p.tb, p.tile);
+    }
     double* scratch = g->scratch;
     bool owned = false;
     if (!scratch) {
@@ -189,7 +196,6 @@ int stencil_run(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_s
     } else if (scratch == g->data) {
         return STENCIL_EINVAL;
     }
-    Plan p = plan_for(h, ctx.g, T, ctx.st);
     if (p.kernel == STENCIL_KERNEL_BLOCKED) {
         if (!jacobi_blocked_supported(h, ctx.g))
             rc = STENCIL_EUNSUPPORTED;
@@ -234,6 +240,7 @@ int stencil_destroy(stencil_handle h)
     cudaFree(h->d_off);
     cudaFree(h->d_status);
     cudaFree(h->wave_ws);
+    cudaFree(h->dia_ws);
     delete h;
     return STENCIL_OK;
 }

@@ -22,6 +22,10 @@ struct stencil_handle_s {
     void* wave_ws = nullptr;
     size_t wave_ws_bytes = 0;
     int wave_epoch = 0;
+    // workspace of the split-tiled (diamond) Jacobi kernel: the per-level edge
+    // bands of every tile, owned by the handle and grown on demand
+    void* dia_ws = nullptr;
+    size_t dia_ws_bytes = 0;
     // failure-detection test hook: the next wavefront run never publishes the
     // completion of this tile (2D/3D) or sweep block (1D); its waiters give up
     // after debug_spin polls instead of the default limit
@@ -68,6 +72,12 @@ int gs_plain_run(const RunCtx& ctx, double* u, int64_t T);
 // result ends in a. Returns EUNSUPPORTED if the configuration is not covered.
 int jacobi_blocked_run(const RunCtx& ctx, double* a, double* b, int64_t T, int tb, const int64_t tile[3]);
 bool jacobi_blocked_supported(const stencil_handle_s* h, const Geo& g);
+
+// Split-tiled (diamond) Jacobi: T steps in place on u, bands of H steps,
+// periods of tile[d] points per axis (0 = defaults). Returns EUNSUPPORTED if
+// the configuration or the grid is not covered.
+int jacobi_diamond_run(const RunCtx& ctx, double* u, int64_t T, int H, const int64_t tile[3]);
+bool jacobi_diamond_supported(const stencil_handle_s* h, const Geo& g);
 
 // Time-skewed wavefront Gauss-Seidel: T sweeps in place.
 int gs_wavefront_run(const RunCtx& ctx, double* u, int64_t T, int lanes);

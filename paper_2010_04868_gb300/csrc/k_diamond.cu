@@ -1,0 +1,584 @@
+// Jacobi with split ("diamond") temporal tiles: no redundant work.
+//
+// Section 3.4 runs 1D Jacobi under diamond tiling, each time tile being a
+// trapezoid or an inverted trapezoid, and higher-dimensional Jacobi under a
+// diamond/parallelogram hybrid; unlike the overlapped tiles of the blocked
+// kernel, no point is computed twice. Here the diamond tiling is realised as
+// split tiling in every axis, which suits a GPU better than the hybrid: every
+// tile of a phase is independent, so a phase is one launch and no tile waits
+// for another.
+//
+// Along each used axis the grid is cut into n periods; period c spans
+// [s_c, s_{c+1}) with s_c = floor(c N / n) and holds an A segment
+// [s_c, s_c + W) followed by a B segment [s_c + W, s_{c+1}), where
+// W = ceil((P + 2 H r) / 2) for the period length P and the band height H.
+// Over a band of h <= H steps an A segment shrinks by r per step on each side
+// that has a neighbour (a trapezoid) and a B segment grows by r per step on
+// each side (an inverted trapezoid), so at every level the segments still
+// partition the axis. A tile is one segment per axis; its type says A or B
+// for each axis. The 2^d types run as 2^d phases in lexicographic order
+// (A before B, slowest axis first), one launch each:
+//   * a tile needs, outside its own level-(k-1) region, only values of tiles
+//     that are A in the axes where it is B: an earlier phase;
+//   * those tiles publish, for every level k < h and every axis where they
+//     are A, the 2r points next to each of their edges (the band) in a
+//     workspace array indexed by level, edge, offset and the full-grid
+//     coordinates of the other two axes, so a consumer finds any point of
+//     its ring, corners included, in one place;
+//   * a tile reads its level-0 region from the grid and writes its level-h
+//     region back to the grid, in place: a later phase's base never meets an
+//     earlier phase's output (they differ in an axis where the earlier one is
+//     A and the later B), so no second grid is needed.
+// Inside a tile, levels run between two shared-memory buffers with one CTA
+// barrier per level; the ring of level k is fetched with cp.async while level
+// k is computed. Every point is computed once, with the same descending-order
+// sum and rounding as the plain kernel, so the result equals T plain steps
+// bit for bit.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace gbst {
+
+struct DiaGeo {
+    int N[3];           // extents, slowest first (1 on unused axes)
+    int n[3];           // periods per axis (1 on unused axes)
+    int act[3];         // 1 on used axes
+    int H;              // band height the segment widths are sized for
+    int h;              // steps of this band (1..H)
+    int fw[3];          // shared-memory frame extents (1 on unused axes)
+    int bc;
+    double c;
+    double* band[3];    // per-axis band arrays (nullptr on unused axes)
+    int64_t other[3];   // points of the two other axes
+};
+
+// Ring fetches in flight: the ring of level k is requested while level
+// k - (DIA_AHEAD - 1) is computed, hiding the L2 latency behind that many levels.
+constexpr int DIA_AHEAD = 4;
+
+__device__ __forceinline__ int wrapn(int q, int n)
+{
+    while (q < 0) q += n;
+    while (q >= n) q -= n;
+    return q;
+}
+
+__device__ __forceinline__ void cp_async8(double* dst, const double* src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Walks the points of an e0 x e1 x e2 box (e2 fastest) from index i0 in steps
+// of `stride` without a division per step.
+struct BoxWalk {
+    int x0, x1, x2, d0, d1, d2, e1, e2;
+    __device__ __forceinline__ BoxWalk(int i0, int stride, int e1_, int e2_) : e1(e1_), e2(e2_)
+    {
+        x2 = i0 % e2;
+        x1 = (i0 / e2) % e1;
+        x0 = i0 / (e2 * e1);
+        d2 = stride % e2;
+        d1 = (stride / e2) % e1;
+        d0 = stride / (e2 * e1);
+    }
+    __device__ __forceinline__ void next()
+    {
+        x2 += d2;
+        x1 += d1;
+        x0 += d0;
+        if (x2 >= e2) {
+            x2 -= e2;
+            ++x1;
+        }
+        if (x1 >= e1) {
+            x1 -= e1;
+            ++x0;
+        }
+    }
+};
+
+// Geometry of one tile, per axis (global coordinates, unwrapped).
+struct DiaTile {
+    int lo[3], hi[3];  // level-0 segment
+    int f0[3];         // frame origin
+    int c[3];          // period index
+    int isB[3];        // 1 if the tile is a B segment on this axis
+    int shL[3];        // A only: the left side shrinks (has a neighbour)
+};
+
+__device__ __forceinline__ void dia_tile(const DiaGeo& G, int phase, int R, DiaTile& t)
+{
+    int b = (int)blockIdx.x;
+    int cc[3];
+    cc[2] = b % G.n[2];
+    b /= G.n[2];
+    cc[1] = b % G.n[1];
+    cc[0] = b / G.n[1];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        t.c[d] = cc[d];
+        if (!G.act[d]) {
+            t.lo[d] = 0;
+            t.hi[d] = 1;
+            t.f0[d] = 0;
+            t.isB[d] = 0;
+            t.shL[d] = 0;
+            continue;
+        }
+        const int64_t N = G.N[d], n = G.n[d];
+        const int s0 = (int)(cc[d] * N / n), s1 = (int)((cc[d] + 1) * N / n), P = s1 - s0;
+        const int W = min(P, (P + 2 * G.H * R + 1) / 2);
+        t.isB[d] = (phase >> (2 - d)) & 1;
+        if (!t.isB[d]) {
+            t.lo[d] = s0;
+            t.hi[d] = s0 + W;
+            t.f0[d] = s0 - R;
+            t.shL[d] = (G.bc == BC_PERIODIC || s0 > 0) ? 1 : 0;
+        } else {
+            t.lo[d] = s0 + W;
+            t.hi[d] = s1;
+            t.f0[d] = s0 + W - (G.H + 1) * R;
+            t.shL[d] = 1;
+        }
+    }
+}
+
+// Region of the tile at level k on axis d: [L, U).
+__device__ __forceinline__ void dia_range(const DiaGeo& G, const DiaTile& t, int d, int k, int R, int& L, int& U)
+{
+    if (!G.act[d]) {
+        L = 0;
+        U = 1;
+    } else if (!t.isB[d]) {
+        L = t.lo[d] + (t.shL[d] ? k * R : 0);
+        U = t.hi[d] - k * R;
+    } else {
+        L = t.lo[d] - k * R;
+        U = t.hi[d] + k * R;
+        if (G.bc == BC_CONSTANT && U > G.N[d]) U = G.N[d];
+    }
+}
+
+// Start of level k, edge e in the band array of axis d.
+__device__ __forceinline__ double* dia_band(const DiaGeo& G, int d, int k, int e, int R)
+{
+    return G.band[d] + (((int64_t)k * 2 * G.n[d] + e) * 2 * R) * G.other[d];
+}
+
+// Publish the bands of level k (buffer b) on every axis where the tile is A:
+// the 2r points next to each edge that has a neighbour, over the tile's
+// level-k region on the other two axes.
+template <int DIM, int R>
+__device__ __forceinline__ void dia_export(const DiaGeo& G, const DiaTile& t, int k, const double* b)
+{
+    const int fs1 = G.fw[2], fs0 = G.fw[1] * G.fw[2];
+    int L[3], U[3];
+    if constexpr (DIM == 1) {
+        // 1D: 2r values per side; the band of an edge is 2r consecutive doubles
+        if (t.isB[2] || threadIdx.x >= 4 * R) return;
+        dia_range(G, t, 2, k, R, L[2], U[2]);
+        const int side = threadIdx.x < 2 * R ? 0 : 1, j = threadIdx.x - 2 * R * side;
+        if (side == 0 && !t.shL[2]) return;
+        const int start = side == 0 ? L[2] : U[2] - 2 * R;
+        dia_band(G, 2, k, 2 * t.c[2] + side, R)[j] = b[start + j - t.f0[2]];
+    } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) dia_range(G, t, d, k, R, L[d], U[d]);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (!G.act[d] || t.isB[d]) continue;
+            // band of axis d: 2r x e0 x e1 points (e1 fastest); one warp per (j, row), lanes along e1
+            const int a0 = d == 0 ? 1 : 0, a1 = d == 2 ? 1 : 2;
+            const int e0 = U[a0] - L[a0], e1 = U[a1] - L[a1];
+            const int fsd = d == 0 ? fs0 : (d == 1 ? fs1 : 1);
+            const int fa0 = a0 == 0 ? fs0 : fs1, fa1 = a1 == 1 ? fs1 : 1;
+            const int64_t na1 = G.N[a1];
+            const int rows = 2 * R * e0;
+            for (int side = t.shL[d] ? 0 : 1; side < 2; ++side) {
+                const int start = side == 0 ? L[d] : U[d] - 2 * R;
+                double* dst = dia_band(G, d, k, 2 * t.c[d] + side, R);
+                const double* srcb = b + (start - t.f0[d]) * fsd + (L[a0] - t.f0[a0]) * fa0 + (L[a1] - t.f0[a1]) * fa1;
+                for (int row = warp; row < rows; row += nwarp) {
+                    const int j = row / e0, x0 = row - j * e0;
+                    const int q0 = wrapn(L[a0] + x0, G.N[a0]);
+                    double* drow = dst + (int64_t)j * G.other[d] + q0 * na1;
+                    const double* srow = srcb + j * fsd + x0 * fa0;
+                    for (int x1 = lane; x1 < e1; x1 += 32) drow[wrapn(L[a1] + x1, G.N[a1])] = srow[x1 * fa1];
+                }
+            }
+        }
+    }
+}
+
+// Request the ring of level k (the 2r points beyond the region on every axis
+// where the tile is B, corners included) into buffer b with cp.async.
+template <int DIM, int R>
+__device__ __forceinline__ void dia_import(const DiaGeo& G, const DiaTile& t, int k, double* b)
+{
+    const int fs1 = G.fw[2], fs0 = G.fw[1] * G.fw[2];
+    int L[3], U[3];
+    if constexpr (DIM == 1) {
+        // 1D: 2r values from the A segment on each side
+        if (!t.isB[2] || threadIdx.x >= 4 * R) return;
+        dia_range(G, t, 2, k, R, L[2], U[2]);
+        const int jj = threadIdx.x;
+        const int qd = jj < 2 * R ? L[2] - 2 * R + jj : t.hi[2] + k * R + jj - 2 * R;
+        if (G.bc == BC_CONSTANT && (qd < 0 || qd >= G.N[2])) return;
+        const double* src = jj < 2 * R ? dia_band(G, 2, k, 2 * t.c[2] + 1, R) + jj
+                                       : dia_band(G, 2, k, 2 * ((t.c[2] + 1) % G.n[2]), R) + jj - 2 * R;
+        cp_async8(b + qd - t.f0[2], src);
+    } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) dia_range(G, t, d, k, R, L[d], U[d]);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (!G.act[d] || !t.isB[d]) continue;
+            // slab of axis d: 4r positions on axis d; on other B axes, the region
+            // (axes before d) or the region widened by 2r (axes after d)
+            int lo[3], ex[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = L[a];
+                ex[a] = U[a] - L[a];
+                if (a > d && G.act[a] && t.isB[a]) {
+                    lo[a] -= 2 * R;
+                    ex[a] += 4 * R;
+                }
+            }
+            const int a0 = d == 0 ? 1 : 0, a1 = d == 2 ? 1 : 2;
+            const int e0 = ex[a0], e1 = ex[a1];
+            const int fsd = d == 0 ? fs0 : (d == 1 ? fs1 : 1);
+            const int fa0 = a0 == 0 ? fs0 : fs1, fa1 = a1 == 1 ? fs1 : 1;
+            const int64_t na1 = G.N[a1];
+            const int Uu = t.hi[d] + k * R;  // right end before clipping to the grid
+            const double* left = dia_band(G, d, k, 2 * t.c[d] + 1, R);                // right band of A on the left
+            const double* right = dia_band(G, d, k, 2 * ((t.c[d] + 1) % G.n[d]), R);  // left band of the next A
+            const int rows = 4 * R * e0;
+            for (int row = warp; row < rows; row += nwarp) {
+                const int jj = row / e0, x0 = row - jj * e0;  // jj 0..4r-1: left part, then right part
+                const int qd = jj < 2 * R ? L[d] - 2 * R + jj : Uu + jj - 2 * R;
+                const int qa0 = lo[a0] + x0;
+                if (G.bc == BC_CONSTANT && (qd < 0 || qd >= G.N[d] || qa0 < 0 || qa0 >= G.N[a0]))
+                    continue;  // outside the grid: holds c already
+                const double* srow = (jj < 2 * R ? left + (int64_t)jj * G.other[d]
+                                                 : right + (int64_t)(jj - 2 * R) * G.other[d]) +
+                                     wrapn(qa0, G.N[a0]) * na1;
+                double* drow = b + (qd - t.f0[d]) * fsd + (qa0 - t.f0[a0]) * fa0 + (lo[a1] - t.f0[a1]) * fa1;
+                for (int x1 = lane; x1 < e1; x1 += 32) {
+                    const int qa1 = lo[a1] + x1;
+                    if (G.bc == BC_CONSTANT && (qa1 < 0 || qa1 >= G.N[a1])) continue;
+                    cp_async8(drow + x1 * fa1, srow + wrapn(qa1, G.N[a1]));
+                }
+            }
+        }
+    }
+}
+
+template <int DIM, int SHAPE, int R, int ARITH>
+__global__ void __launch_bounds__(256, (DIM == 2 && SHAPE == STAR && R == 1) ? 4 : 2) k_jacobi_diamond(double* __restrict__ u, DiaGeo G, int phase,
+                                                           WArr<Stn<DIM, SHAPE, R>::K> w)
+{
+    extern __shared__ __align__(16) double sm[];
+    const int F = G.fw[0] * G.fw[1] * G.fw[2];
+    double* const bufA = sm;
+    double* const bufB = sm + ((F + 1) & ~1);
+    auto buf = [&](int k) { return (k & 1) ? bufB : bufA; };  // level k's buffer, no local-memory array
+    const int fs1 = G.fw[2], fs0 = G.fw[1] * G.fw[2];
+    DiaTile t;
+    dia_tile(G, phase, R, t);
+    const int nthr = blockDim.x;
+
+    // ---- level 0: constant boundary cells, the base from the grid, the rings of the first levels
+    if (G.bc == BC_CONSTANT) {
+        BoxWalk it(threadIdx.x, nthr, G.fw[1], G.fw[2]);
+        for (int i = threadIdx.x; i < F; i += nthr, it.next()) {
+            const int q0 = t.f0[0] + it.x0, q1 = t.f0[1] + it.x1, q2 = t.f0[2] + it.x2;
+            if (q0 < 0 || q0 >= G.N[0] || q1 < 0 || q1 >= G.N[1] || q2 < 0 || q2 >= G.N[2]) {
+                bufA[i] = G.c;
+                bufB[i] = G.c;
+            }
+        }
+    }
+    {
+        int L[3], U[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) dia_range(G, t, d, 0, R, L[d], U[d]);
+        const int e2 = U[2] - L[2], e1 = U[1] - L[1];
+        const int cnt = (U[0] - L[0]) * e1 * e2;
+        BoxWalk it(threadIdx.x, nthr, e1, e2);
+        for (int i = threadIdx.x; i < cnt; i += nthr, it.next()) {
+            const int q0 = L[0] + it.x0, q1 = L[1] + it.x1, q2 = L[2] + it.x2;
+            const int64_t gi = ((int64_t)wrapn(q0, G.N[0]) * G.N[1] + wrapn(q1, G.N[1])) * G.N[2] + wrapn(q2, G.N[2]);
+            cp_async8(bufA + (q0 - t.f0[0]) * fs0 + (q1 - t.f0[1]) * fs1 + (q2 - t.f0[2]), u + gi);
+        }
+    }
+    // groups: {base, ring 0}, ring 1, ..., ring DIA_AHEAD-1 (empty groups past the band)
+    dia_import<DIM, R>(G, t, 0, bufA);
+    cp_async_commit();
+#pragma unroll
+    for (int k = 1; k < DIA_AHEAD; ++k) {
+        if (k < G.h) dia_import<DIM, R>(G, t, k, buf(k));
+        cp_async_commit();
+    }
+    cp_async_wait<DIA_AHEAD - 1>();
+    __syncthreads();
+
+    if constexpr (DIM == 1) {
+        // 1D: every per-level quantity is a tile constant plus a multiple of k
+        const int f0 = t.f0[2], lo = t.lo[2], hi = t.hi[2], N = G.N[2], shL = t.shL[2];
+        const bool isB = t.isB[2], clip = G.bc == BC_CONSTANT;
+        const int64_t lvl = (int64_t)4 * G.n[2] * R;  // band doubles per level
+        const int tid = threadIdx.x, side = tid < 2 * R ? 0 : 1, j = tid - 2 * R * side;
+        const bool io = tid < 4 * R;
+        // export (A): edge 2c + side; import (B): right band of A_c, left band of A_{c+1}
+        double* const ex = G.band[2] + (2 * t.c[2] + side) * 2 * R + j;
+        const double* const im =
+            G.band[2] + (side == 0 ? (2 * t.c[2] + 1) * 2 * R : 2 * ((t.c[2] + 1) % G.n[2]) * 2 * R) + j;
+        for (int k = 1; k <= G.h; ++k) {
+            const double* src = buf(k - 1);
+            double* dst = buf(k);
+            if (io && !isB && (side == 1 || shL)) {
+                const int km = k - 1;
+                const int q = side == 0 ? lo + km * R + j : hi - km * R - 2 * R + j;
+                ex[km * lvl] = src[q - f0];
+            }
+            const int kr = k + DIA_AHEAD - 1;
+            if (io && isB && kr < G.h) {
+                const int q = side == 0 ? lo - kr * R - 2 * R + j : hi + kr * R + j;
+                if (!clip || (q >= 0 && q < N)) cp_async8(buf(kr) + (q - f0), im + kr * lvl);
+            }
+            cp_async_commit();
+            const int L = isB ? lo - k * R : lo + (shL ? k * R : 0);
+            const int U = isB ? (clip ? min(hi + k * R, N) : hi + k * R) : hi - k * R;
+            for (int i = L - f0 + tid; i < U - f0; i += nthr)
+                dst[i] = update_interior<DIM, SHAPE, R, ARITH, false>(src, i, fs0, fs1, w);
+            cp_async_wait<DIA_AHEAD - 1>();  // ring k has landed
+            __syncthreads();
+        }
+    } else {
+    // ---- levels 1..h: publish level k-1, compute level k, request ring k + DIA_AHEAD - 1
+    for (int k = 1; k <= G.h; ++k) {
+        const double* src = buf(k - 1);
+        double* dst = buf(k);
+        dia_export<DIM, R>(G, t, k - 1, src);
+        {
+            // the ring goes to positions no level before it reads or writes
+            const int kr = k + DIA_AHEAD - 1;
+            if (kr < G.h) dia_import<DIM, R>(G, t, kr, buf(kr));
+            cp_async_commit();
+        }
+        int L[3], U[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) dia_range(G, t, d, k, R, L[d], U[d]);
+        const int e2 = U[2] - L[2], e1 = U[1] - L[1];
+        const int cnt = (U[0] - L[0]) * e1 * e2;
+        const int base = (L[0] - t.f0[0]) * fs0 + (L[1] - t.f0[1]) * fs1 + (L[2] - t.f0[2]);
+        // two points per thread and pass, so that two independent sums are in flight
+        BoxWalk it(threadIdx.x, nthr, e1, e2);
+        int i = threadIdx.x;
+        for (; i + nthr < cnt; i += 2 * nthr) {
+            const int pa = base + it.x0 * fs0 + it.x1 * fs1 + it.x2;
+            it.next();
+            const int pb = base + it.x0 * fs0 + it.x1 * fs1 + it.x2;
+            it.next();
+            const double va = update_interior<DIM, SHAPE, R, ARITH, false>(src, pa, fs0, fs1, w);
+            const double vb = update_interior<DIM, SHAPE, R, ARITH, false>(src, pb, fs0, fs1, w);
+            dst[pa] = va;
+            dst[pb] = vb;
+        }
+        if (i < cnt) {
+            const int pa = base + it.x0 * fs0 + it.x1 * fs1 + it.x2;
+            dst[pa] = update_interior<DIM, SHAPE, R, ARITH, false>(src, pa, fs0, fs1, w);
+        }
+        cp_async_wait<DIA_AHEAD - 1>();  // ring k has landed
+        __syncthreads();
+    }
+    }
+
+    // ---- write level h back to the grid
+    {
+        const double* b = buf(G.h);
+        int L[3], U[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) dia_range(G, t, d, G.h, R, L[d], U[d]);
+        const int e2 = U[2] - L[2], e1 = U[1] - L[1];
+        const int cnt = (U[0] - L[0]) * e1 * e2;
+        BoxWalk it(threadIdx.x, nthr, e1, e2);
+        for (int i = threadIdx.x; i < cnt; i += nthr, it.next()) {
+            const int q0 = L[0] + it.x0, q1 = L[1] + it.x1, q2 = L[2] + it.x2;
+            const int64_t gi = ((int64_t)wrapn(q0, G.N[0]) * G.N[1] + wrapn(q1, G.N[1])) * G.N[2] + wrapn(q2, G.N[2]);
+            u[gi] = b[(q0 - t.f0[0]) * fs0 + (q1 - t.f0[1]) * fs1 + (q2 - t.f0[2])];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+bool jacobi_diamond_supported(const stencil_handle_s* h, const Geo& g)
+{
+    (void)g;
+    return h->method == JACOBI && !h->field && plain_specialised(h->dim, h->shape, h->r);
+}
+
+// Tiling of one run: periods per axis, band height, frame extents. Returns
+// EUNSUPPORTED when an extent is too short for even one step per band.
+int diamond_geometry(const stencil_handle_s* h, const Geo& g, int H, const int64_t tile_in[3], DiaGeo& G,
+                     size_t& smem, size_t& ws_doubles)
+{
+    const int dim = h->dim, r = h->r;
+    const int64_t N[3] = {g.n0, g.n1, g.n2};
+    int nsm = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t P[3] = {tile_in ? tile_in[0] : 0, tile_in ? tile_in[1] : 0, tile_in ? tile_in[2] : 0};
+    if (H <= 0) H = dim == 1 ? 32 : (dim == 2 ? 16 : 4);
+    for (int d = 0; d < 3; ++d) {
+        if (N[d] >= (int64_t(1) << 30)) return STENCIL_EUNSUPPORTED;
+        G.act[d] = d >= 3 - dim;
+        G.N[d] = (int)N[d];
+        if (!G.act[d]) {
+            P[d] = 1;
+            continue;
+        }
+        if (P[d] <= 0) P[d] = dim == 1 ? std::max<int64_t>((N[d] + 4 * nsm - 1) / (4 * nsm), 64 * r) : (dim == 2 ? 88 : 24);
+        if (P[d] < 2 * r) P[d] = 2 * r;
+    }
+    // periods: as many as fit the target length, at least one
+    int64_t pmin = INT64_MAX;
+    for (int d = 0; d < 3; ++d) {
+        if (!G.act[d]) {
+            G.n[d] = 1;
+            continue;
+        }
+        int64_t n = N[d] / P[d];
+        if (n < 1) n = 1;
+        if (n > (1 << 30)) return STENCIL_EUNSUPPORTED;
+        G.n[d] = (int)n;
+        pmin = std::min(pmin, N[d] / n);
+    }
+    // every A segment must keep 2r points per side through the band: P >= 2 H r
+    H = (int)std::min<int64_t>(H, pmin / (2 * r));
+    if (H < 1) return STENCIL_EUNSUPPORTED;
+    G.H = H;
+    G.h = H;
+    int64_t tiles = 1;
+    for (int d = 0; d < 3; ++d) {
+        G.fw[d] = 1;
+        G.band[d] = nullptr;
+        G.other[d] = 1;
+        if (!G.act[d]) continue;
+        int64_t fw = 0;
+        for (int64_t c = 0; c < G.n[d]; ++c) {
+            const int64_t s0 = c * N[d] / G.n[d], s1 = (c + 1) * N[d] / G.n[d], Pc = s1 - s0;
+            const int64_t W = std::min<int64_t>(Pc, (Pc + 2 * (int64_t)H * r + 1) / 2);
+            fw = std::max(fw, std::max(W + 2 * r, Pc - W + 2 * (int64_t)(H + 1) * r));
+        }
+        if (fw > (1 << 20)) return STENCIL_EUNSUPPORTED;
+        G.fw[d] = (int)fw;
+        tiles *= G.n[d];
+    }
+    const int64_t F = (int64_t)G.fw[0] * G.fw[1] * G.fw[2];
+    smem = (size_t)(((F + 1) & ~int64_t(1)) + F) * sizeof(double);
+    if (smem > 227 * 1024 || tiles > 0x7fffffffLL) return STENCIL_EUNSUPPORTED;
+    ws_doubles = 0;
+    for (int d = 0; d < 3; ++d) {
+        if (!G.act[d]) continue;
+        G.other[d] = (N[0] * N[1] * N[2]) / N[d];
+        ws_doubles += (size_t)H * 2 * G.n[d] * 2 * r * G.other[d];
+    }
+    G.bc = h->bc;
+    G.c = h->c;
+    return STENCIL_OK;
+}
+
+// Grow the handle's band workspace to at least `bytes` (never inside a capture).
+static int diamond_workspace(stencil_handle_s* h, size_t bytes, cudaStream_t st)
+{
+    if (h->dia_ws_bytes >= bytes) return STENCIL_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return STENCIL_EUNSUPPORTED;
+    }
+    if (h->dia_ws) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return STENCIL_ECUDA;
+        cudaFree(h->dia_ws);
+        h->dia_ws = nullptr;
+        h->dia_ws_bytes = 0;
+    }
+    if (cudaMalloc(&h->dia_ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return STENCIL_ENOMEM;
+    }
+    h->dia_ws_bytes = bytes;
+    return STENCIL_OK;
+}
+
+template <int DIM, int SHAPE, int R>
+static int diamond_bands(const RunCtx& ctx, double* u, int64_t T, int H, const int64_t tile[3])
+{
+    constexpr int K = Stn<DIM, SHAPE, R>::K;
+    WArr<K> w;
+    for (int q = 0; q < K; ++q) w.w[q] = ctx.h->w_desc[q];
+    DiaGeo G;
+    size_t smem = 0, wsd = 0;
+    int rc = diamond_geometry(ctx.h, ctx.g, H, tile, G, smem, wsd);
+    if (rc) return rc;
+    rc = diamond_workspace(ctx.h, wsd * sizeof(double), ctx.st);
+    if (rc) return rc;
+    double* p = (double*)ctx.h->dia_ws;
+    for (int d = 0; d < 3; ++d) {
+        if (!G.act[d]) continue;
+        G.band[d] = p;
+        p += (size_t)G.H * 2 * G.n[d] * 2 * R * G.other[d];
+    }
+    auto kern = ctx.h->arith == ARITH_FMA ? k_jacobi_diamond<DIM, SHAPE, R, ARITH_FMA>
+                                          : k_jacobi_diamond<DIM, SHAPE, R, ARITH_UNFUSED>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return STENCIL_ECUDA;
+    const unsigned nblk = (unsigned)((int64_t)G.n[0] * G.n[1] * G.n[2]);
+    // threads per tile: one level of a 1D tile is at most fw points, so small
+    // CTAs there (more tiles resident per SM, a cheaper barrier per level)
+    const int nthr = DIM == 1 ? (G.fw[2] <= 128 ? 128 : 256) : 256;
+    // phases: types over the used axes in lexicographic order, A (0) before B (1), slowest axis first
+    int phases[8], np = 0;
+    for (int m = 0; m < 8; ++m) {
+        bool ok = true;
+        for (int d = 0; d < 3; ++d)
+            if (((m >> (2 - d)) & 1) && !G.act[d]) ok = false;
+        if (ok) phases[np++] = m;
+    }
+    for (int64_t done = 0; done < T;) {
+        G.h = (int)std::min<int64_t>(G.H, T - done);
+        for (int q = 0; q < np; ++q) {
+            kern<<<nblk, nthr, smem, ctx.st>>>(u, G, phases[q], w);
+            g_launches++;
+            if (cudaGetLastError() != cudaSuccess) return STENCIL_ECUDA;
+        }
+        done += G.h;
+    }
+    return STENCIL_OK;
+}
+
+int jacobi_diamond_run(const RunCtx& ctx, double* u, int64_t T, int H, const int64_t tile[3])
+{
+    const stencil_handle_s* h = ctx.h;
+#define X(D, S, R) \
+    if (h->dim == D && h->shape == S && h->r == R) return diamond_bands<D, S, R>(ctx, u, T, H, tile);
+    X(1, STAR, 1) X(1, STAR, 2) X(1, STAR, 3) X(1, STAR, 4)
+    X(2, STAR, 1) X(2, BOX, 1) X(2, STAR, 2) X(2, BOX, 2)
+    X(3, STAR, 1) X(3, BOX, 1) X(3, STAR, 2)
+#undef X
+    return STENCIL_EUNSUPPORTED;
+}
+
+}  // namespace gbst

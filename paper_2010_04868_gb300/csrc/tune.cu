@@ -3,10 +3,11 @@
 // The paper picks blocking sizes by trying every power-of-two, symmetric
 // size and keeping the fastest (Section 4.1), and leaves an auto-tuner to
 // future work (Section 6). Here the tuner measures instead of guessing:
-//   * Jacobi: the plain per-step kernel and the temporally blocked kernel
-//     over a small set of tiles and depths T_b are each timed for a few
-//     steps on private buffers of the run's extents; the fastest per step
-//     wins, a plan other than plain only if it is more than 3% faster. On GB300 the FP64 pipe, not HBM, bounds large grids, so the plain
+//   * Jacobi: the plain per-step kernel, the temporally blocked kernel over a
+//     small set of tiles and depths T_b, and the split (diamond) tiles over a
+//     few periods and band heights are each timed for a few steps on private
+//     buffers of the run's extents; the fastest per step wins, a plan other
+//     than plain only if it is more than 3% faster. On GB300 the FP64 pipe, not HBM, bounds large grids, so the plain
 //     kernel usually wins there and blocking wins where launches dominate.
 //   * Gauss-Seidel: the wavefront kernel whenever it is legal (constant
 //     boundary); it was faster than per-sweep execution in every measured
@@ -103,7 +104,21 @@ std::vector<Plan> jacobi_candidates(const stencil_handle_s* h, const Geo& g, int
 {
     std::vector<Plan> c;
     c.push_back(Plan{STENCIL_KERNEL_PLAIN, 1, {0, 0, 0}});
-    if (!jacobi_blocked_supported(h, g) || T < 2) return c;
+    if (T < 2) return c;
+    // split (diamond) tiles: no redundant work, so they compete where the FP64 pipe binds
+    if (jacobi_diamond_supported(h, g)) {
+        auto dia = [&](int H, int64_t t0, int64_t t1, int64_t t2) {
+            if (H <= T) c.push_back(Plan{STENCIL_KERNEL_DIAMOND, H, {t0, t1, t2}});
+        };
+        if (h->dim == 1) {
+            for (int H : {54, 100}) dia(H / h->r > 0 ? H / h->r : 1, 0, 0, 0);
+            dia(100 / h->r > 0 ? 100 / h->r : 1, 0, 0, (g.n2 + 303) / 304 < 64 ? 64 : (g.n2 + 303) / 304);
+        } else if (h->dim == 2) {
+            dia(16, 0, 80, 80);
+            dia(16, 0, 88, 88);
+        }
+    }
+    if (!jacobi_blocked_supported(h, g)) return c;
     auto add = [&](int tb, int64_t t0, int64_t t1, int64_t t2) {
         if (tb <= T) c.push_back(Plan{STENCIL_KERNEL_BLOCKED, tb, {t0, t1, t2}});
     };
@@ -193,7 +208,8 @@ Plan plan_for(const stencil_handle_s* hc, const Geo& g, int64_t T, cudaStream_t 
         return default_plan(h, g);
     }
     if (getenv("STENCIL_NO_TUNE")) return default_plan(h, g);
-    if (!jacobi_blocked_supported(h, g)) return default_plan(h, g);  // the plain kernel is the only candidate
+    if (!jacobi_blocked_supported(h, g) && !jacobi_diamond_supported(h, g))
+        return default_plan(h, g);  // the plain kernel is the only candidate
     const size_t n = (size_t)(g.n0 * g.n1 * g.n2);
     double *a = nullptr, *b = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {

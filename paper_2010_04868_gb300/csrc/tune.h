@@ -5,9 +5,9 @@
 namespace gbst {
 
 struct Plan {
-    int kernel;       // STENCIL_KERNEL_PLAIN / BLOCKED / WAVEFRONT
-    int tb;           // temporal block depth (blocked) or sweeps per warp (wavefront)
-    int64_t tile[3];  // tile extents for the blocked kernel, slowest first
+    int kernel;       // STENCIL_KERNEL_PLAIN / BLOCKED / WAVEFRONT / DIAMOND
+    int tb;           // temporal block depth (blocked, diamond) or sweeps per warp (wavefront)
+    int64_t tile[3];  // tile extents (blocked) or period lengths (diamond), slowest first
 };
 
 // The plan a run uses: the handle's fixed plan if set, else the tuned one.
