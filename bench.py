@@ -37,10 +37,15 @@ STENCILS = (("2d5p", 0, 5), ("2d9p", 1, 9))   # name, shape id, K
 # all three instructions, 152 SMs, i.e. 529.9 Gop/s at the 2070 MHz maximum clock.
 FP64_OPS_PER_SM_CLK = 1.684
 N_SM = 152
-# DRAM bytes (read + write) per launch of the plain 2D 9-point kernel on this
-# workload, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
-# the algorithmic figure is 16 B per point update, 268.4 MB per launch.
-NCU_TRAFFIC = {"Jacobi 2D 9P plain": 134_247_168 + 94_438_912}
+KERNEL_NAMES = {1: "plain", 2: "blocked", 3: "wavefront", 4: "diamond"}
+# DRAM bytes (read + write) per launch on this workload, from ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by stencil and plan
+# (kernel, T_b, tile); a plan without a capture reports null. Plain: one step
+# per launch, algorithmically 16 B per point update (268.4 MB per launch).
+# Split (diamond) tiles: four launches (one per tile type) per band of T_b steps; the figure is the
+# band's total over four, so it includes the per-level edge bands the tiles exchange through L2/HBM.
+NCU_TRAFFIC = {("2d9p", "plain", 1, (0, 0, 0)): 134_247_168 + 94_438_912,
+               ("2d9p", "diamond", 16, (0, 88, 88)): (464_250_112 + 175_210_752) // 4}
 
 
 def _args():
@@ -74,6 +79,14 @@ def aggregate(total_ms, world, dist=None, device=None):
 def job_value(updates_per_rank_step, world, ms_per_step):
     """Whole-job throughput in GStencil/s: every rank processes its own replica in ms_per_step."""
     return world * updates_per_rank_step / (ms_per_step * 1e-3) / 1e9
+
+
+def algorithmic_bytes_per_launch(plan, launches):
+    """16 B per point per pass over the grid (one read, one write): every step for the plain kernel,
+    every T_b steps for the blocked and split-tiled kernels."""
+    tb = max(1, plan["tb"]) if plan["kernel"] in ("blocked", "diamond") else 1
+    passes = -(-T_STEPS // tb)
+    return 16 * N_SIDE * N_SIDE * passes // max(1, launches)
 
 
 def weights(k):
@@ -187,6 +200,11 @@ def run_ours(args):
         if rc != 0:
             raise RuntimeError("device status after warm-up: " + S.strerror(rc))
 
+    plans = {}
+    for name, _, _ in STENCILS:
+        k, tb, tile = work[name]["st"].plan(work[name]["u"], T_STEPS)
+        plans[name] = {"kernel": KERNEL_NAMES.get(k, str(k)), "tb": tb, "tile": list(tile)}
+
     sampler = ClockSampler(local)
     sampler.start()
     times = {name: 0.0 for name, _, _ in STENCILS}
@@ -225,12 +243,13 @@ def run_ours(args):
     achieved = ops_per_launch / (avg_launch_ms * 1e-3) / 1e9
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak = FP64_OPS_PER_SM_CLK * N_SM * sm_mhz * 1e6 / 1e9
-    roofline = {"bound": "alu", "kernel": "Jacobi 2D %dP (%d launches per run)" % (k_dom, launches_dom), "achieved": round(achieved, 2),
-                "peak": round(peak, 2), "unit": "Gop/s (FP64 lane operations)", "frac": round(achieved / peak, 4),
-                "traffic": None,
-                "hbm_algorithmic_gbs": round(16.0 * N_SIDE * N_SIDE / (avg_launch_ms * 1e-3) / 1e9, 1)}
-    if launches_dom != T_STEPS:
-        roofline["hbm_algorithmic_gbs"] = None
+    pd = plans[dom]
+    traffic = NCU_TRAFFIC.get((dom, pd["kernel"], pd["tb"], tuple(pd["tile"])))
+    roofline = {"bound": "alu",
+                "kernel": "Jacobi 2D %dP %s (%d launches per run)" % (k_dom, pd["kernel"], launches_dom),
+                "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "Gop/s (FP64 lane operations)",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": algorithmic_bytes_per_launch(pd, launches_dom)}
 
     per_stencil = {name: round(N_SIDE * N_SIDE * T_STEPS * args.steps / (times[name] * 1e-3) / 1e9, 3)
                    for name, _, _ in STENCILS}
@@ -269,7 +288,7 @@ def run_ours(args):
                                    "T=1000 each, autotuned kernel", "grids": "2 x 4096^2", "T": T_STEPS,
                        "l2": "inputs (2 x 128 MiB grid + scratch) exceed L2; 512 MiB flush between steps",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "per_stencil_gstencil_s": per_stencil, "plain_kernel_gstencil_s": plain,
+            "per_stencil_gstencil_s": per_stencil, "plain_kernel_gstencil_s": plain, "plans": plans,
             "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches),
             "e2e": e2e, "cpu_baseline": cpu,
         }

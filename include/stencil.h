@@ -177,6 +177,19 @@ int stencil_run_batch(const stencil_handle* h, const stencil_grid* g, const int6
  */
 int stencil_set_coeff_field(stencil_handle h, const double* field, const int64_t ext[3]);
 
+/*
+ * The kernel family and parameters stencil_run(h, g, T, stream) would use:
+ * the fixed plan of stencil_set_plan, or the autotuned one (tuning first, on
+ * private buffers, if this (stencil, extents, T) class has no cached plan;
+ * inside a stream capture the cached or static default). kernel receives a
+ * STENCIL_KERNEL_* value other than AUTO, tb the temporal block depth (or
+ * sweeps per warp), tile the tile extents or periods (slowest first; 0 =
+ * the kernel's default). Any output pointer may be NULL. Returns STENCIL_OK,
+ * EINVAL or a CUDA error code.
+ */
+int stencil_get_plan(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_stream, int* kernel, int* tb,
+                     int64_t tile[3]);
+
 /* Bytes of workspace stencil_run needs for g (0 for Gauss-Seidel). */
 int stencil_workspace_bytes(stencil_handle h, const stencil_grid* g, size_t* bytes);
 

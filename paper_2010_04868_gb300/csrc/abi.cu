@@ -148,6 +148,23 @@ int stencil_set_coeff_field(stencil_handle h, const double* field, const int64_t
     return STENCIL_OK;
 }
 
+int stencil_get_plan(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_stream, int* kernel, int* tb,
+                     int64_t tile[3])
+{
+    int rc = check_grid(h, g);
+    if (rc) return rc;
+    if (T < 0) return STENCIL_EINVAL;
+    Plan p = plan_for(h, make_geo(h->dim, g->ext), T, (cudaStream_t)cuda_stream);
+    if (h->method == STENCIL_GAUSS_SEIDEL && p.kernel == STENCIL_KERNEL_WAVEFRONT &&
+        !gs_wavefront_supported(h, make_geo(h->dim, g->ext)))
+        p.kernel = STENCIL_KERNEL_PLAIN;
+    if (kernel) *kernel = p.kernel;
+    if (tb) *tb = p.tb;
+    if (tile)
+        for (int d = 0; d < 3; ++d) tile[d] = p.tile[d];
+    return STENCIL_OK;
+}
+
 int stencil_workspace_bytes(stencil_handle h, const stencil_grid* g, size_t* bytes)
 {
     if (!bytes) return STENCIL_EINVAL;

@@ -31,7 +31,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgb300ste
 #: Every entry point that include/stencil.h declares.
 EXPORTS = ("stencil_create", "stencil_set_plan", "stencil_run", "stencil_run_batch", "stencil_workspace_bytes",
            "stencil_status", "stencil_destroy", "stencil_strerror", "stencil_run_host", "stencil_launch_count",
-           "stencil_run_noalloc", "stencil_debug_inject_stall", "stencil_set_coeff_field",
+           "stencil_run_noalloc", "stencil_debug_inject_stall", "stencil_set_coeff_field", "stencil_get_plan",
            "life_workspace_bytes", "life_run", "lcs_workspace_bytes", "lcs_run", "lcs_status")
 
 #: Largest grid (points) stencil_run_noalloc accepts: its fixed workspace holds 2^21 doubles.
@@ -67,6 +67,8 @@ def load(path: str = LIB_PATH):
     lib.stencil_run_noalloc.argtypes = [P, ctypes.POINTER(stencil_grid), I64, P]
     lib.stencil_debug_inject_stall.argtypes = [P, I64, I]
     lib.stencil_set_coeff_field.argtypes = [P, P, ctypes.POINTER(I64)]
+    lib.stencil_get_plan.argtypes = [P, ctypes.POINTER(stencil_grid), I64, P, ctypes.POINTER(I), ctypes.POINTER(I),
+                                     ctypes.POINTER(I64)]
     lib.life_workspace_bytes.argtypes = [ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_size_t)]
     lib.life_run.argtypes = [P, ctypes.POINTER(I64), I, ctypes.c_uint32, ctypes.c_uint32, I64, I, P, P]
     lib.lcs_workspace_bytes.argtypes = [I64, I64, I, ctypes.POINTER(ctypes.c_size_t)]
@@ -134,6 +136,15 @@ def stencil_set_coeff_field(h, field_ptr, ext):
     """Bind per-point weights (device pointer to K x N doubles, canonical term-major); None unbinds."""
     e = (ctypes.c_int64 * 3)(*(list(ext) + [1] * (3 - len(ext))))
     return check(load().stencil_set_coeff_field(h, field_ptr, e), "stencil_set_coeff_field")
+
+
+def stencil_get_plan(h, grid: stencil_grid, T, stream_ptr=None):
+    """(kernel, tb, tile) that stencil_run would use for this grid and T (tuning first if needed)."""
+    k, tb = ctypes.c_int(), ctypes.c_int()
+    tile = (ctypes.c_int64 * 3)()
+    check(load().stencil_get_plan(h, ctypes.byref(grid), int(T), stream_ptr, ctypes.byref(k), ctypes.byref(tb), tile),
+          "stencil_get_plan")
+    return k.value, tb.value, tuple(tile)
 
 
 def stencil_workspace_bytes(h, grid: stencil_grid) -> int:
@@ -236,6 +247,10 @@ class Stencil:
     def run(self, u, T, scratch=None, stream=None):
         stencil_run(self.handle, self.grid(u, scratch), T, _stream_ptr(stream))
         return u
+
+    def plan(self, u, T, stream=None):
+        """(kernel, tb, tile) that run(u, T) would use."""
+        return stencil_get_plan(self.handle, self.grid(u), T, _stream_ptr(stream))
 
     def status(self, stream=None) -> int:
         return stencil_status(self.handle, _stream_ptr(stream))

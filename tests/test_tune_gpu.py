@@ -35,8 +35,27 @@ def test_tune_cache_file(tmp_path):
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr
     lines = [json.loads(x) for x in cache.read_text().splitlines()]
-    assert len(lines) == 1 and lines[0]["kernel"] in (1, 2)
+    assert len(lines) == 1 and lines[0]["kernel"] in (1, 2, 4)
     # a second process reads the entry instead of tuning again
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr
     assert len(cache.read_text().splitlines()) == 1
+
+
+def test_get_plan_reports_fixed_and_tuned_plans():
+    import torch
+    from paper_2010_04868_gb300 import stencil as S
+    st = S.Stencil(2, 1, 1, [1.0 / 9] * 9)
+    u = torch.rand(200, 300, dtype=torch.float64, device="cuda")
+    st.set_plan(S.STENCIL_KERNEL_DIAMOND, 6, (0, 40, 50))
+    assert st.plan(u, 30) == (S.STENCIL_KERNEL_DIAMOND, 6, (0, 40, 50))
+    st.set_plan(S.STENCIL_KERNEL_AUTO)
+    k, tb, tile = st.plan(u, 30)
+    assert k in (S.STENCIL_KERNEL_PLAIN, S.STENCIL_KERNEL_BLOCKED, S.STENCIL_KERNEL_DIAMOND) and tb >= 1
+    assert st.plan(u, 30) == (k, tb, tile)          # cached: the same answer without tuning again
+    gs = S.Stencil(2, 0, 1, [0.2] * 5, S.STENCIL_GAUSS_SEIDEL)
+    assert gs.plan(u, 10)[0] == S.STENCIL_KERNEL_WAVEFRONT
+    gp = S.Stencil(2, 0, 1, [0.2] * 5, S.STENCIL_GAUSS_SEIDEL, S.STENCIL_BC_PERIODIC)
+    assert gp.plan(u, 10)[0] in (S.STENCIL_KERNEL_WAVEFRONT, S.STENCIL_KERNEL_PLAIN)
+    for x in (st, gs, gp):
+        x.close()
