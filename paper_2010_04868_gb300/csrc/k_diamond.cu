@@ -468,6 +468,268 @@ __global__ void __launch_bounds__(256, (DIM == 2 && SHAPE == STAR && R == 1) ? 4
     }
 }
 
+// ---------------------------------------------------------- 1D, concurrent ---
+//
+// The same split tiles in 1D, but with the A and B segments of one period
+// advancing together in one persistent launch, so that every step has all of
+// a level's points in flight (the phase launches above hold half of them, and
+// a 1D level has few points per SM). CTA c owns period c: its A segment (the
+// trapezoid) computes level s at step s, its B segment (the inverted
+// trapezoid, right of A) computes level s - HEX_LAG at the same step, one CTA
+// barrier per step. B's ring comes from A's right band (shared memory) and
+// from the left band of the next period's A (published by CTA c + 1). At the
+// end of a band, A's next base takes its two edges from B tops: its own and
+// the previous period's (published by CTA c - 1). The grid is read once at
+// the start and written once at the end; every level stays on chip.
+//
+// Warp 0 does each step's edge I/O (bands, ring) and no stencil work, so that
+// its latencies hide behind the other warps' FP64 chains; those synchronise on
+// a named barrier once per step and count the steps in shared memory. The last
+// warp does all inter-CTA traffic and no stencil work either, decoupled from
+// the steps: it releases this CTA's A levels as the step count passes them,
+// acquires the next period's progress, and copies the next period's A left
+// band into a shared ring of 8 levels as soon as it is published and a slot is
+// free, marking each level ready with a CTA-scope release; B's ring is written
+// from it HEX_LAG steps after the level, so the L2 round trips never sit on a
+// step. Every CTA must be resident at once (the launch checks the occupancy);
+// every wait is bounded and records STENCIL_ETIMEOUT instead of hanging.
+constexpr int HEX_LAG = 16;
+constexpr int SPIN_LIMIT_DIAMOND = 1 << 23;  // x ~0.25-0.5 us per poll: a wait gives up after two to four seconds
+
+struct HexGeo {
+    int N, n, H, bc;
+    double c;
+    int64_t T;
+    int fwA, fwB;        // frame widths of the A and B segments
+    int* flagA;          // n: sequence number of the last A level whose left band is published
+    int* flagB;          // n: last band whose B top is published
+    double* aband;       // n x H x 2r: left band of A per level of the current band
+    double* btop;        // n x H r: the part of B's top right of the period
+    int* status;
+    int spin;
+};
+
+__device__ __forceinline__ int hex_ld_acquire(const int* f)
+{
+    int x;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(x) : "l"(f) : "memory");
+    return x;
+}
+
+__device__ __forceinline__ bool hex_wait_ge(const int* f, int v, int spin)
+{
+    for (int it = 0; it < spin; ++it) {
+        if (hex_ld_acquire(f) >= v) return true;
+        __nanosleep(it < 64 ? 32 : 256);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void hex_release(int* f, int v)
+{
+    __threadfence();
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_cta(const int* p)
+{
+    int x;
+    asm volatile("ld.acquire.cta.shared.b32 %0, [%1];" : "=r"(x) : "r"((uint32_t)__cvta_generic_to_shared(p)) : "memory");
+    return x;
+}
+
+__device__ __forceinline__ void st_release_cta(int* p, int v)
+{
+    asm volatile("st.release.cta.shared.b32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+
+template <int R, int ARITH>
+__global__ void __launch_bounds__(512) k_jacobi_hex1d(double* __restrict__ u, HexGeo G, WArr<2 * R + 1> w)
+{
+    extern __shared__ __align__(16) double sm[];
+    __shared__ int step_done;   // compute warps: steps of the band completed
+    __shared__ int ring_ready;  // comm warp: levels of the band in the ring
+    const int c = blockIdx.x, n = G.n, N = G.N;
+    const int s0 = (int)((int64_t)c * N / n), s1 = (int)((int64_t)(c + 1) * N / n), P = s1 - s0;
+    const int W = min(P, (P + 2 * G.H * R + 1) / 2);
+    const int loA = s0, hiA = s0 + W, loB = s0 + W, hiB = s1;
+    const bool clip = G.bc == BC_CONSTANT;
+    const bool hasL = !clip || c > 0;      // A shrinks on its left; its left band has a consumer
+    const bool hasR = !clip || c < n - 1;  // B has an A segment on its right
+    const int fA = loA - R, fB = loB - (G.H + 1) * R;  // frame origins (global coordinates, unwrapped)
+    double* const A0 = sm;
+    double* const A1 = A0 + G.fwA;
+    double* const B0 = A1 + G.fwA;
+    double* const B1 = B0 + G.fwB;
+    double* const arb = B1 + G.fwB;         // H x 2r: A's right band per level
+    double* const rvb = arb + G.H * 2 * R;  // 8 x 2r: the next period's A left band, ring of levels
+    double* const alb = rvb + 8 * 2 * R;    // H x 2r: A's left band per level, staged for the comm warp
+    auto Ab = [&](int g) { return (g & 1) ? A1 : A0; };
+    auto Bb = [&](int g) { return (g & 1) ? B1 : B0; };
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int ncomp = nthr - 32;  // compute threads; the last warp communicates
+    const bool comm = tid >= ncomp;
+    const int lane = tid - ncomp;
+    const int cl = (c + n - 1) % n, cr = (c + 1) % n;
+    const int seqH = G.H + 1;
+    bool ok = true;
+
+    // ---- the grid's values into buffer 0; cells outside the grid hold c in both buffers
+    for (int i = tid; i < G.fwA; i += nthr) {
+        const int q = fA + i;
+        if (q < 0 || q >= N) {
+            A0[i] = G.c;
+            A1[i] = G.c;
+        } else if (q >= loA && q < hiA) {
+            A0[i] = u[q];
+        }
+    }
+    for (int i = tid; i < G.fwB; i += nthr) {
+        const int q = fB + i;
+        if (clip && (q < 0 || q >= N)) {
+            B0[i] = G.c;
+            B1[i] = G.c;
+        } else if (q >= loB && q < hiB) {
+            B0[i] = u[q < N ? q : q - N];
+        }
+    }
+
+    int g0 = 0;  // global level at the start of the band (buffer parity)
+    for (int64_t done = 0, b = 0; done < G.T; ++b) {
+        const int h = (int)min((int64_t)G.H, G.T - done);
+        if (tid == 0) {
+            step_done = 0;
+            ring_ready = 0;
+        }
+        __syncthreads();
+        if (!comm) {
+            // ---- compute warps: step s = A at level s and B at level s - HEX_LAG, one named barrier per step
+            int ring_known = 0;  // I/O warp: ring levels known to be ready
+            for (int s = 1; s <= h + HEX_LAG; ++s) {
+                const int kB = s - HEX_LAG, kx = s - 1, kr = s - HEX_LAG;
+                const int aL = loA + (hasL ? s * R : 0) - fA, nA = s <= h ? hiA - s * R - fA - aL : 0;
+                const int bL = loB - kB * R - fB;
+                const int nB = (kB >= 1 && kB <= h) ? (clip ? min(hiB + kB * R, N) : hiB + kB * R) - fB - bL : 0;
+                // offsets into the shared array itself, so that every access is a shared-memory one
+                const int oAs = ((g0 + s - 1) & 1) * G.fwA, oAd = ((g0 + s) & 1) * G.fwA;
+                const int oBs = 2 * G.fwA + ((g0 + kB - 1) & 1) * G.fwB, oBd = 2 * G.fwA + ((g0 + kB) & 1) * G.fwB;
+                // warp 0 does this step's shared-memory and band I/O below; warps 1.. the points
+                for (int i = tid - 32; i < nA + nB; i += ncomp - 32) {
+                    if (i < 0) break;
+                    const bool inA = i < nA;
+                    const int ps = inA ? oAs + aL + i : oBs + bL + i - nA;
+                    const int pd = inA ? oAd + aL + i : oBd + bL + i - nA;
+                    sm[pd] = update_interior<1, STAR, R, ARITH, false>(sm, ps, 0, 0, w);
+                }
+                // A's bands of level s - 1: the left one staged for the previous period, the right one for B
+                if (kx < h && tid < 4 * R) {
+                    const double* a = Ab(g0 + kx);
+                    if (tid < 2 * R) {
+                        if (hasL) alb[kx * 2 * R + tid] = a[loA + kx * R + tid - fA];
+                    } else {
+                        const int j = tid - 2 * R;
+                        arb[kx * 2 * R + j] = a[hiA - (kx + 2) * R + j - fA];
+                    }
+                }
+                // B's ring of level s - HEX_LAG (read by level s - HEX_LAG + 1 next step)
+                if (kr >= 0 && kr < h && tid < 4 * R) {
+                    double* bb = Bb(g0 + kr);
+                    if (tid < 2 * R) {
+                        bb[loB - (kr + 2) * R + tid - fB] = arb[kr * 2 * R + tid];
+                    } else if (hasR) {
+                        const int j = tid - 2 * R;
+                        // the comm warp runs several levels ahead: acquire only when the known count runs out
+                        for (int it = 0; ring_known <= kr; ++it) {
+                            ring_known = ld_acquire_cta(&ring_ready);
+                            if (ring_known > kr) break;
+                            if (it >= G.spin) {
+                                ok = false;
+                                break;
+                            }
+                            __nanosleep(32);
+                        }
+                        bb[hiB + kr * R + j - fB] = rvb[(kr & 7) * 2 * R + j];
+                    }
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(ncomp) : "memory");
+                if (tid == 0) st_release_cta(&step_done, s);
+            }
+        } else {
+            // ---- comm warp: release this CTA's A levels as the compute warps finish them, fetch
+            // the next period's A levels into the ring as it publishes them and slots free up
+            int rel = 0;    // levels of this CTA released
+            int lv = 0;     // next level to fetch
+            int known = 0;  // next period's last acquired sequence number
+            int it = 0;
+            while ((hasL && rel < h) || (hasR && lv < h)) {
+                int sd = 0;  // read by one lane and broadcast: the warp's control flow stays uniform
+                if (lane == 0) sd = ld_acquire_cta(&step_done);
+                sd = __shfl_sync(0xffffffffu, sd, 0);
+                bool progressed = false;
+                // level k's band is staged at step k + 1: copy to global, then release
+                if (hasL && rel < h && sd >= rel + 1) {
+                    const int upto = min(sd, h);
+                    for (int i = lane; i < (upto - rel) * 2 * R; i += 32)
+                        G.aband[((int64_t)c * G.H + rel) * 2 * R + i] = alb[rel * 2 * R + i];
+                    __syncwarp();
+                    if (lane == 0) hex_release(G.flagA + c, (int)b * seqH + upto);
+                    rel = upto;
+                    progressed = true;
+                }
+                // slot lv & 7 held level lv - 8, consumed at step lv - 8 + HEX_LAG
+                if (hasR && lv < h && sd >= lv - 8 + HEX_LAG) {
+                    if (known < (int)b * seqH + lv + 1) {
+                        int v = 0;
+                        if (lane == 0) v = hex_ld_acquire(G.flagA + cr);
+                        known = __shfl_sync(0xffffffffu, v, 0);
+                        __syncwarp();  // the other lanes' loads come after lane 0's acquire
+                    }
+                    if (known >= (int)b * seqH + lv + 1) {
+                        // every level the next period has published whose slot is free, in one batch
+                        const int last = min(min(known - (int)b * seqH - 1, h - 1), sd + 8 - HEX_LAG);
+                        for (int l = lv; l <= last; ++l)
+                            if (lane < 2 * R)
+                                rvb[(l & 7) * 2 * R + lane] = __ldcg(G.aband + ((int64_t)cr * G.H + l) * 2 * R + lane);
+                        __syncwarp();
+                        if (lane == 0) st_release_cta(&ring_ready, last + 1);
+                        lv = last + 1;
+                        progressed = true;
+                    }
+                }
+                if (!progressed) {
+                    __nanosleep(64);
+                    if (++it >= G.spin) {
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // ---- band end: B's top right part to the next period, A's next base from the B tops
+        const double* btop = Bb(g0 + h);
+        double* abase = Ab(g0 + h);
+        if (hasR)
+            for (int i = tid; i < h * R; i += nthr) G.btop[(int64_t)c * G.H * R + i] = btop[hiB + i - fB];
+        for (int i = tid; i < h * R; i += nthr) abase[loB - h * R + i - fA] = btop[loB - h * R + i - fB];
+        __syncthreads();
+        if (tid == 0) {
+            if (hasR) hex_release(G.flagB + c, (int)b + 1);
+            if (hasL && !hex_wait_ge(G.flagB + cl, (int)b + 1, G.spin)) ok = false;
+        }
+        __syncthreads();
+        if (hasL)
+            for (int i = tid; i < h * R; i += nthr) abase[loA + i - fA] = __ldcg(G.btop + (int64_t)cl * G.H * R + i);
+        done += h;
+        g0 += h;
+    }
+    __syncthreads();
+    // ---- the period's final values back to the grid
+    for (int i = loA + tid; i < hiA; i += nthr) u[i] = Ab(g0)[i - fA];
+    for (int i = loB + tid; i < hiB; i += nthr) u[i] = Bb(g0)[i - fB];
+    if (!ok) atomicExch(G.status, DEV_TIMEOUT);
+}
+
 // ------------------------------------------------------------------ host side
 
 bool jacobi_diamond_supported(const stencil_handle_s* h, const Geo& g)
@@ -570,9 +832,83 @@ static int diamond_workspace(stencil_handle_s* h, size_t bytes, cudaStream_t st)
     return STENCIL_OK;
 }
 
+// 1D with every period resident at once: the concurrent kernel, one launch.
+// Returns EUNSUPPORTED (nothing enqueued) when the periods do not all fit.
+template <int R>
+static int diamond_hex1d(const RunCtx& ctx, double* u, int64_t T, int H, const int64_t tile[3])
+{
+    const stencil_handle_s* h = ctx.h;
+    const int64_t N = ctx.g.n2;
+    int nsm = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (N >= (int64_t(1) << 30)) return STENCIL_EUNSUPPORTED;
+    const int64_t P = tile && tile[2] > 0 ? tile[2] : (N + nsm - 1) / nsm;
+    int64_t n = N / (P > 0 ? P : 1);
+    if (n < 1) n = 1;
+    if (n > 4 * nsm) return STENCIL_EUNSUPPORTED;
+    const int64_t pmin = N / n;
+    if (H <= 0) H = 100;
+    H = (int)std::min<int64_t>(H, pmin / (2 * R));
+    if (H < 1) return STENCIL_EUNSUPPORTED;
+    int64_t fwA = 0, fwB = 0, pmax = 0;
+    for (int64_t c = 0; c < n; ++c) {
+        const int64_t s0 = c * N / n, s1 = (c + 1) * N / n, Pc = s1 - s0;
+        const int64_t W = std::min<int64_t>(Pc, (Pc + 2 * (int64_t)H * R + 1) / 2);
+        fwA = std::max(fwA, W + 2 * R);
+        fwB = std::max(fwB, Pc - W + 2 * (int64_t)(H + 1) * R);
+        pmax = std::max(pmax, Pc);
+    }
+    fwA = (fwA + 1) & ~int64_t(1);
+    fwB = (fwB + 1) & ~int64_t(1);
+    const size_t smem = (size_t)(2 * fwA + 2 * fwB + (int64_t)H * 4 * R + 8 * 2 * R) * sizeof(double);
+    if (smem > 200 * 1024) return STENCIL_EUNSUPPORTED;
+    // one communication warp plus compute warps for about one point per thread and step
+    const int nthr = pmax > 384 ? 512 : (pmax > 192 ? 288 : 160);
+    auto kern = h->arith == ARITH_FMA ? k_jacobi_hex1d<R, ARITH_FMA> : k_jacobi_hex1d<R, ARITH_UNFUSED>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return STENCIL_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nthr, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return STENCIL_ECUDA;
+    }
+    if ((int64_t)per_sm * nsm < n) return STENCIL_EUNSUPPORTED;  // every CTA waits on its neighbours
+    // workspace: flags, A left bands, B top parts
+    const size_t flag_bytes = (size_t)((2 * n * sizeof(int) + 255) & ~size_t(255));
+    const size_t bytes = flag_bytes + (size_t)n * H * 3 * R * sizeof(double);
+    int rc = diamond_workspace(const_cast<stencil_handle_s*>(h), bytes, ctx.st);
+    if (rc) return rc;
+    HexGeo G;
+    G.N = (int)N;
+    G.n = (int)n;
+    G.H = H;
+    G.bc = h->bc;
+    G.c = h->c;
+    G.T = T;
+    G.fwA = (int)fwA;
+    G.fwB = (int)fwB;
+    G.flagA = (int*)h->dia_ws;
+    G.flagB = G.flagA + n;
+    G.aband = (double*)((char*)h->dia_ws + flag_bytes);
+    G.btop = G.aband + (size_t)n * H * 2 * R;
+    G.status = h->d_status;
+    G.spin = SPIN_LIMIT_DIAMOND;
+    WArr<2 * R + 1> w;
+    for (int q = 0; q < 2 * R + 1; ++q) w.w[q] = h->w_desc[q];
+    if (cudaMemsetAsync(h->dia_ws, 0, 2 * n * sizeof(int), ctx.st) != cudaSuccess) return STENCIL_ECUDA;
+    kern<<<(unsigned)n, nthr, smem, ctx.st>>>(u, G, w);
+    g_launches++;
+    return cuda_rc(cudaGetLastError());
+}
+
 template <int DIM, int SHAPE, int R>
 static int diamond_bands(const RunCtx& ctx, double* u, int64_t T, int H, const int64_t tile[3])
 {
+    if constexpr (DIM == 1) {
+        const int rc = diamond_hex1d<R>(ctx, u, T, H, tile);
+        if (rc != STENCIL_EUNSUPPORTED) return rc;
+    }
     constexpr int K = Stn<DIM, SHAPE, R>::K;
     WArr<K> w;
     for (int q = 0; q < K; ++q) w.w[q] = ctx.h->w_desc[q];

@@ -2,7 +2,9 @@
 
 The diamond plan tiles every used axis into A segments (trapezoids in
 space-time) and B segments (inverted trapezoids), runs the 2^dim tile types of
-a band as separate phases and works in place. The cases cover one to many
+a band as separate phases and works in place; in 1D, when every period fits
+on the GPU at once, one persistent launch runs A and B of each period
+together (neighbouring periods exchange edge values through flags). The cases cover one to many
 periods per axis, ragged periods, band heights that the shortest period
 forces down, T below, at and above the band height, radii 1..4, both
 boundaries and both rounding modes.
@@ -27,6 +29,8 @@ CASES = [
     (1, "star", 2, (3001,), 5, (0, 0, 97)),
     (1, "star", 3, (500,), 6, (0, 0, 64)),
     (1, "star", 4, (777,), 3, (0, 0, 100)),
+    (1, "star", 1, (20000,), 8, (0, 0, 16)),       # 1250 periods: more than can be resident, phase launches
+    (1, "star", 2, (9000,), 40, (0, 0, 0)),        # one period per SM: the concurrent kernel
     (2, "star", 1, (2, 3), 2, (0, 0, 0)),
     (2, "star", 1, (130, 258), 4, (0, 40, 64)),
     (2, "star", 1, (131, 257), 6, (0, 0, 0)),
