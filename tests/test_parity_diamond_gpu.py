@@ -119,15 +119,17 @@ def test_periodic_3d_diamond_equals_plain():
     assert bits_equal(got, plain), first_diff(got, plain)
 
 
-def test_diamond_run_replays_in_a_cuda_graph():
-    """After one run has sized the workspace, a run captured into a CUDA graph replays to the same grid."""
+@pytest.mark.parametrize("dim,ext,H,periods", [(2, (300, 257), 4, (0, 64, 64)), (1, (30011,), 40, (0, 0, 0))])
+def test_diamond_run_replays_in_a_cuda_graph(dim, ext, H, periods):
+    """After one run has sized the workspace, a run captured into a CUDA graph replays to the same grid
+    (2D: the phase launches; 1D: the concurrent kernel with its flag reset)."""
     import torch
     from paper_2010_04868_gb300 import stencil as S
-    w, u0 = case(2, "star", 1, (300, 257), seed=3)
-    T = 11
-    ref = oracle_run(u0, T, 2, "star", 1, w, "jacobi", "constant", 0.0, "fma")
-    st = S.Stencil(2, 0, 1, list(w), S.STENCIL_JACOBI)
-    st.set_plan(DIAMOND, 4, (0, 64, 64))
+    w, u0 = case(dim, "star", 1, ext, seed=3)
+    T = 11 if dim == 2 else 97
+    ref = oracle_run(u0, T, dim, "star", 1, w, "jacobi", "constant", 0.0, "fma")
+    st = S.Stencil(dim, 0, 1, list(w), S.STENCIL_JACOBI)
+    st.set_plan(DIAMOND, H, periods)
     u = torch.from_numpy(u0.copy()).cuda()
     st.run(u, T)
     assert st.status() == 0
