@@ -212,38 +212,72 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
     }
 }
 
-// Radius 1, three warps per sweep block. One warp issues at most one FP64
-// instruction per ~64 clocks, so the single-warp kernel spends three of those
-// per step. Here the three terms of a lane's update are issued by three warps
-// (on three SM sub-partitions), a pipeline through shared memory with one CTA
-// barrier per step:
-//   warp 0  term +1 (the first product) of point m = s + 2
-//   warp 1  term  0 (first fused add)   of point m = s + 1
-//   warp 2  term -1 (newest value)      of point m = s, and the output
-// At loop step s every warp reads only values written before the previous
-// barrier: its predecessor's partial sum (double-buffered by point parity) and
-// lane k-1's outputs from a ring of the last 8 steps. Lane k holds sweep t0+k
-// at x = m - 4k; the skew 4 = 2r + 2 makes the previous-sweep value warp 0
-// needs for point m (lane k-1's output at x + 1) appear at step m - 3, one
-// step before warp 0 handles m. Lane 0 of warps 0 and 1 takes the grid's
-// values (the previous sweep block's output) from 32-value chunks as above.
-__device__ __forceinline__ void bar_sync96() { asm volatile("bar.sync 1, 96;" ::: "memory"); }
+// 1D, radius 1, decoupled: one warp issues only the newest-value FMA chain.
+//
+// Lane k holds sweep t0 + k at x = j - 33k at step j. With that skew, the two
+// previous-sweep terms of a point (lane k - 1's outputs at x and x + 1, made
+// at steps j - 33 and j - 32) are known two batches of 16 steps before the
+// point is due, so they can be summed away from the chain:
+//   warps 1-6 (producers) form P = w(+1) u'(x+1) (+) w(0) u'(x) for the next
+//             batch of 16 steps, each warp a share of the steps, all 32 lanes
+//             (unrolled, so that their sums overlap);
+//   warp 0 (the chain) does the 16 dependent updates u(x) = P (+) w(-1) u(x-1)
+//             of the current batch from registers;
+// one CTA barrier per batch instead of one per step. The chain's outputs go to
+// a shared ring of 3 batches (the producers read the two before the current
+// one); lane 0's previous-sweep values are the previous block's outputs, which
+// warp 7 fetches from the grid two batches ahead (through a register), behind
+// the same progress words as above, stores the last lane's outputs (the block's
+// final sweep) and publishes this block's progress every 4 batches, so that no
+// load, store or fence of global memory sits in the FP64 warps' batches. The sum keeps the
+// descending order and rounding of every other kernel.
+constexpr int W4_S = 33, W4_D = 16, W4_ROWS = 3 * W4_D;
 
-template <int ARITH>
-__global__ void __launch_bounds__(96) k_gs1d_wave3(double* __restrict__ u, int64_t n, double c, WArr<3> w, int64_t T,
-                                                   unsigned long long* progress, int* ticket, int* status,
-                                                   unsigned tag, WaitCfg wc)
+// Partial sums of steps D0 .. D1 - 1 of batch m for every lane (k = lane), unrolled so that the
+// independent sums of the steps overlap. rbm = (16 m) mod 48, the ring row of the batch's first step.
+template <int ARITH, int D0, int D1>
+__device__ __forceinline__ void w4_produce(int64_t m, int64_t mmax, int rbm, int L, int64_t n, double c,
+                                           const WArr<3>& w, const double (*O)[32], double (*Pb)[W4_D][32],
+                                           const double* BOT)
 {
-    constexpr int S = 4;
+    if (m > mmax) return;
+    const int k = threadIdx.x & 31;
+    const int64_t x0 = W4_D * m - (int64_t)W4_S * k;
+#pragma unroll
+    for (int d = D0; d < D1; ++d) {
+        const int64_t x = x0 + d;
+        if (k < L && x >= 0 && x < n) {
+            double v0, v1;
+            if (k == 0) {
+                v0 = BOT[x & 63];
+                v1 = x + 1 < n ? BOT[(x + 1) & 63] : c;
+            } else {
+                // lane k - 1's outputs at steps j - 33 and j - 32: ring rows rbm + d - 33 and - 32 (mod 48)
+                int r0 = rbm + d + (W4_ROWS - W4_S), r1 = r0 + 1;
+                r0 = r0 >= W4_ROWS ? r0 - W4_ROWS : r0;
+                r1 = r1 >= W4_ROWS ? r1 - W4_ROWS : r1;
+                v0 = O[r0][k - 1];
+                v1 = O[r1][k - 1];  // lane k - 1 wrote c there when x + 1 >= n
+            }
+            Pb[m & 1][d][k] = acc_step<ARITH>(__dmul_rn(w.w[0], v1), w.w[1], v0);
+        }
+    }
+}
+
+// Warp roles: 0 the chain; 1-6 the partial sums (a warp issues at most one FP64
+// instruction per ~64 clocks, so the 32 per batch are spread over six warps);
+// 7 lane 0's grid values, the block's final sweep to the grid, and progress.
+template <int ARITH>
+__global__ void __launch_bounds__(256) k_gs1d_wave4(double* __restrict__ u, int64_t n, double c, WArr<3> w, int64_t T,
+                                                    unsigned long long* progress, int* ticket, int* status,
+                                                    unsigned tag, WaitCfg wc)
+{
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ int s_b;
-    __shared__ double acc0[2][32], acc1[2][32], outr[8][32];
+    __shared__ double O[W4_ROWS][32];      // outputs: row = step mod 48, column = lane
+    __shared__ double Pb[2][W4_D][32];     // producers' partial sums: batch parity, step in batch, lane
+    __shared__ double BOT[64];             // lane 0's previous-sweep values, by position mod 64
     if (threadIdx.x == 0) s_b = atomicAdd(ticket, 1);
-    for (int q = threadIdx.x; q < 8 * 32; q += 96) (&outr[0][0])[q] = c;
-    for (int q = threadIdx.x; q < 2 * 32; q += 96) {
-        (&acc0[0][0])[q] = 0.0;
-        (&acc1[0][0])[q] = 0.0;
-    }
     __syncthreads();
     const int b = s_b;
     const int64_t nB = (T + 31) / 32;
@@ -253,92 +287,95 @@ __global__ void __launch_bounds__(96) k_gs1d_wave3(double* __restrict__ u, int64
     unsigned long long* mine = progress + b;
     const bool publish = b != wc.stall;
     const unsigned long long mytag = (unsigned long long)tag << PROG_SHIFT;
-    int64_t known = b > 0 ? 0 : INT64_MAX;
-    auto need_upto = [&](int64_t upto) {
-        if (lane == 0 && upto > known) known = wait_progress(prev, upto, tag, status, wc.spin);
+    const int64_t jmax = n - 1 + (int64_t)W4_S * (L - 1), mmax = jmax / W4_D;
+    int64_t known = b > 0 ? 0 : INT64_MAX;  // warp 7: positions the previous block has finalised
+
+    // warp 7: positions [16m, 16m + 32) of the previous block's output, fetched into a register
+    // one batch before they are stored into BOT
+    auto bot_fetch = [&](int64_t m) -> double {
+        const int64_t lo = W4_D * m;
+        if (lo >= n) return c;
+        const int64_t need = lo + 32 < n ? lo + 32 : n;
+        if (lane == 0 && need > known) known = wait_progress(prev, need, tag, status, wc.spin);
         __syncwarp();
+        const int64_t x = lo + lane;
+        return x < n ? __ldcg(u + x) : c;
     };
-    auto load_chunk = [&](int64_t ch) -> double {
-        const int64_t p = ch * 32 + lane;
-        return (p >= 0 && p < n) ? __ldcg(u + p) : c;
+    auto bot_store = [&](int64_t m, double v) {
+        if (W4_D * m < n) BOT[(W4_D * m + lane) & 63] = v;
     };
-    const int64_t steps = n + (int64_t)S * (L - 1);
-    // The step loop runs in chunks of 32 steps starting at s0 = -32 (the first
-    // two steps that matter are s = -2, -1: pipeline fill). With s0 a multiple
-    // of 32, every ring slot, buffer parity and shuffle lane below is a
-    // compile-time constant of the unrolled step j, and each warp's grid
-    // position crosses into its next 32-value chunk at a fixed j.
-    if (warp < 2) {
-        // warp 0: term +1 of point s + 2, grid position s + 3; warp 1: term 0 of point s + 1, position s + 1
-        const int OFF = warp == 0 ? 3 : 1;
-        double cur = c;                // chunk (s0 + OFF) >> 5 at the start of a chunk of steps
-        need_upto(n < 32 ? n : 32);
-        double nxt = load_chunk(0);
-        for (int64_t s0 = -32; s0 < steps; s0 += 32) {
-            const int64_t c0 = s0 >> 5;
-            const bool first = s0 < 0;  // outputs of steps < 0 do not exist: previous-sweep values are c
-            if (warp == 0) {
+    auto produce = [&](int64_t m) {
+        const int rbm = (int)((W4_D * m) % W4_ROWS);
+        switch (warp) {
+            case 1: w4_produce<ARITH, 0, 3>(m, mmax, rbm, L, n, c, w, O, Pb, BOT); break;
+            case 2: w4_produce<ARITH, 3, 6>(m, mmax, rbm, L, n, c, w, O, Pb, BOT); break;
+            case 3: w4_produce<ARITH, 6, 9>(m, mmax, rbm, L, n, c, w, O, Pb, BOT); break;
+            case 4: w4_produce<ARITH, 9, 12>(m, mmax, rbm, L, n, c, w, O, Pb, BOT); break;
+            case 5: w4_produce<ARITH, 12, 14>(m, mmax, rbm, L, n, c, w, O, Pb, BOT); break;
+            case 6: w4_produce<ARITH, 14, 16>(m, mmax, rbm, L, n, c, w, O, Pb, BOT); break;
+            default: break;
+        }
+    };
+
+    // prologue: the previous block's first 48 positions, the partial sums of batch 0
+    double nextbot = c;
+    if (warp == 7) {
+        bot_store(0, bot_fetch(0));
+        bot_store(1, bot_fetch(1));
+        nextbot = bot_fetch(2);
+    }
+    __syncthreads();
+    produce(0);
+    __syncthreads();
+
+    double nw = c;  // chain: this lane's previous output (the left neighbour of its next point)
+    for (int64_t m = 0; m <= mmax + 1; ++m) {
+        if (warp == 0) {
+            if (m <= mmax) {
+                const int k = lane;
+                double p[W4_D];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    if (j == 29) {     // position s0 + j + 3 enters chunk c0 + 1
-                        cur = nxt;
-                        const int64_t upto = (c0 + 3) * 32;
-                        need_upto(upto < n ? upto : n);
-                        nxt = load_chunk(c0 + 2);
+                for (int d = 0; d < W4_D; ++d) p[d] = Pb[m & 1][d][k];
+                const int row0 = (int)((W4_D * m) % W4_ROWS);
+                const int64_t x0 = W4_D * m - (int64_t)W4_S * k;
+#pragma unroll
+                for (int d = 0; d < W4_D; ++d) {
+                    const int64_t x = x0 + d;
+                    double o = c;
+                    if (k < L && x >= 0 && x < n) {
+                        o = acc_step<ARITH>(p[d], w.w[2], nw);
+                        nw = o;
                     }
-                    const double bottom = __shfl_sync(FULL, cur, (j + 3) & 31);
-                    double v = (first || lane == 0) ? c : outr[(j + 7) & 7][lane - 1];
-                    if (lane == 0 && s0 + j + 3 < n) v = bottom;
-                    acc0[j & 1][lane] = __dmul_rn(w.w[0], v);
-                    bar_sync96();
+                    O[row0 + d][k] = o;
                 }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    if (j == 31) {     // position s0 + j + 1 enters chunk c0 + 1
-                        cur = nxt;
-                        const int64_t upto = (c0 + 3) * 32;
-                        need_upto(upto < n ? upto : n);
-                        nxt = load_chunk(c0 + 2);
+            }
+        } else if (warp < 7) {
+            produce(m + 1);
+        } else {
+            bot_store(m + 2, nextbot);  // read by batch m + 2's partial sums, next iteration
+            nextbot = bot_fetch(m + 3);
+            if (m >= 1 && m - 1 <= mmax) {
+                // the last lane's outputs of batch m - 1 (the block's final sweep) to the grid;
+                // this block's progress every 4 batches
+                if (lane < W4_D) {
+                    const int64_t j = W4_D * (m - 1) + lane, x = j - (int64_t)W4_S * (L - 1);
+                    if (x >= 0 && x < n) u[x] = O[j % W4_ROWS][L - 1];
+                }
+                if ((m & 3) == 3 && publish) {
+                    __syncwarp();
+                    const int64_t xl = W4_D * (m - 1) + W4_D - 1 - (int64_t)W4_S * (L - 1);
+                    if (lane == 0 && xl >= 0) {
+                        __threadfence();
+                        st_release64(mine, mytag | (unsigned long long)(xl + 1 < n ? xl + 1 : n));
                     }
-                    const double bottom = __shfl_sync(FULL, cur, (j + 1) & 31);
-                    double v = (first || lane == 0) ? c : outr[(j + 5) & 7][lane - 1];
-                    if (lane == 0 && s0 + j + 1 >= 0 && s0 + j + 1 < n) v = bottom;
-                    acc1[(j + 1) & 1][lane] = acc_step<ARITH>(acc0[(j + 1) & 1][lane], w.w[1], v);
-                    bar_sync96();
                 }
             }
-            (void)OFF;
         }
-    } else {
-        double nw = c;  // this lane's previous output
-        const bool top = lane == L - 1;
-        for (int64_t s0 = -32; s0 < steps; s0 += 32) {
-            if (s0 < 0) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) bar_sync96();
-                continue;
-            }
-            const int64_t x0 = s0 - (int64_t)S * lane;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int64_t x = x0 + j;
-                const double acc = acc_step<ARITH>(acc1[j & 1][lane], w.w[2], nw);
-                const bool inside = x >= 0 && x < n;
-                nw = inside ? acc : c;
-                outr[j & 7][lane] = nw;
-                if (top && inside) u[x] = acc;
-                bar_sync96();
-            }
-            if (top && publish && ((s0 >> 5) & 1) && x0 + 31 >= 0) {
-                __threadfence();
-                st_release64(mine, mytag | (unsigned long long)(x0 + 32 < n ? x0 + 32 : n));
-            }
-        }
-        if (top && publish) {
-            __threadfence();
-            st_release64(mine, mytag | (unsigned long long)n);
-        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 224 && publish) {  // warp 7, after its last stores
+        __threadfence();
+        st_release64(mine, mytag | (unsigned long long)n);
     }
 }
 
@@ -764,11 +801,11 @@ static int wave_1d(const RunCtx& ctx, double* u, int64_t T, bool prepare_only = 
         WArr<3> w3;
         for (int q = 0; q < 3; ++q) w3.w[q] = w.w[q];
         if (h->arith == ARITH_FMA)
-            k_gs1d_wave3<ARITH_FMA><<<(unsigned)nB, 96, 0, ctx.st>>>(u, ctx.g.n2, h->c, w3, T, progress, ticket,
-                                                                      h->d_status, tag, wc);
+            k_gs1d_wave4<ARITH_FMA><<<(unsigned)nB, 256, 0, ctx.st>>>(u, ctx.g.n2, h->c, w3, T, progress, ticket,
+                                                                       h->d_status, tag, wc);
         else
-            k_gs1d_wave3<ARITH_UNFUSED><<<(unsigned)nB, 96, 0, ctx.st>>>(u, ctx.g.n2, h->c, w3, T, progress, ticket,
-                                                                          h->d_status, tag, wc);
+            k_gs1d_wave4<ARITH_UNFUSED><<<(unsigned)nB, 256, 0, ctx.st>>>(u, ctx.g.n2, h->c, w3, T, progress, ticket,
+                                                                           h->d_status, tag, wc);
     } else {
         launch_gs1d_wave<R>(ctx, u, T, w, progress, ticket, tag, wc);
     }
