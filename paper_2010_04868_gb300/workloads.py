@@ -2,6 +2,7 @@
 
     python -m paper_2010_04868_gb300.workloads --config NAME [--kernel auto|plain|blocked|wavefront|diamond]
                                                [--T STEPS] [--reps N] [--tb TB] [--tile A,B,C]
+                                               [--ext E0,E1,...]
 
 Prints one JSON line per configuration: GStencil/s (point updates per second),
 the FP64-operation rate against the FP64 pipe's measured peak, and the
@@ -96,14 +97,15 @@ def config_grid(name):
     return inputs.grid(inputs.SEED_BASE + 10 + list(CONFIGS).index(name), ext)
 
 
-def run(name, kernel="auto", T=None, reps=2, tb=0, tile=(0, 0, 0), sm_mhz=2070.0):
+def run(name, kernel="auto", T=None, reps=2, tb=0, tile=(0, 0, 0), sm_mhz=2070.0, ext=None):
     import torch
 
     from . import stencil as S
-    dim, shape, method, ext, T0, bc, _ = CONFIGS[name]
+    dim, shape, method, ext0, T0, bc, _ = CONFIGS[name]
+    ext = tuple(ext) if ext else ext0
     r = RADIUS.get(name, 1)
     T = T0 if T is None else T
-    u0 = torch.from_numpy(config_grid(name)).cuda()
+    u0 = torch.from_numpy(config_grid(name) if ext == ext0 else inputs.grid(inputs.SEED_BASE + 10, ext)).cuda()
     st = S.Stencil(dim, shape, r, config_weights(name), method, bc)
     if name in FIELD:
         st.set_field(torch.from_numpy(config_field(name)).cuda())
@@ -268,6 +270,7 @@ def main():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--tb", type=int, default=0)
     ap.add_argument("--tile", default="0,0,0")
+    ap.add_argument("--ext", default="", help="override the grid extents, e.g. 1048576 or 512,512 (small cases)")
     a = ap.parse_args()
     names = list(CONFIGS) + ["batch3d", "life", "lcs"] if a.config == "all" else a.config.split(",")
     tile = tuple(int(x) for x in a.tile.split(","))
@@ -280,7 +283,8 @@ def main():
             for k in (("dp", "bits") if a.kernel == "auto" else (a.kernel,)):
                 print(json.dumps(run_lcs(k, reps=a.reps)), flush=True)
         else:
-            print(json.dumps(run(n, a.kernel, a.T, a.reps, a.tb, tile)), flush=True)
+            ext = tuple(int(x) for x in a.ext.split(",")) if a.ext else None
+            print(json.dumps(run(n, a.kernel, a.T, a.reps, a.tb, tile, ext=ext)), flush=True)
 
 
 if __name__ == "__main__":
