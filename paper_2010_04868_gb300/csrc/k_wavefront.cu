@@ -226,10 +226,11 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
 // one CTA barrier per batch instead of one per step. The chain's outputs go to
 // a shared ring of 3 batches (the producers read the two before the current
 // one); lane 0's previous-sweep values are the previous block's outputs, which
-// warp 7 fetches from the grid two batches ahead (through a register), behind
-// the same progress words as above, stores the last lane's outputs (the block's
-// final sweep) and publishes this block's progress every 4 batches, so that no
-// load, store or fence of global memory sits in the FP64 warps' batches. The sum keeps the
+// warp 7 fetches from the grid two batches ahead with cp.async (a CTA barrier
+// waits for a warp's outstanding register loads, not for cp.async), behind the
+// same progress words as above, stores the last lane's outputs (the block's
+// final sweep) and publishes this block's progress every 4 batches, with the
+// fence at the start of the next batch where it overlaps the chain. The sum keeps the
 // descending order and rounding of every other kernel.
 constexpr int W4_S = 33, W4_D = 16, W4_ROWS = 3 * W4_D;
 
@@ -290,20 +291,26 @@ __global__ void __launch_bounds__(256) k_gs1d_wave4(double* __restrict__ u, int6
     const int64_t jmax = n - 1 + (int64_t)W4_S * (L - 1), mmax = jmax / W4_D;
     int64_t known = b > 0 ? 0 : INT64_MAX;  // warp 7: positions the previous block has finalised
 
-    // warp 7: positions [16m, 16m + 32) of the previous block's output, fetched into a register
-    // one batch before they are stored into BOT
-    auto bot_fetch = [&](int64_t m) -> double {
+    // warp 7: positions [16m, 16m + 32) of the previous block's output into BOT by cp.async (the
+    // CTA barrier does not wait for it, a register load would hold the barrier for an L2 round trip)
+    auto bot_fetch = [&](int64_t m) {
         const int64_t lo = W4_D * m;
-        if (lo >= n) return c;
+        if (lo >= n) return;
         const int64_t need = lo + 32 < n ? lo + 32 : n;
         if (lane == 0 && need > known) known = wait_progress(prev, need, tag, status, wc.spin);
         __syncwarp();
         const int64_t x = lo + lane;
-        return x < n ? __ldcg(u + x) : c;
+        double* dst = BOT + (x & 63);
+        if (x < n) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                         "l"(u + x)
+                         : "memory");
+        } else {
+            *dst = c;
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    auto bot_store = [&](int64_t m, double v) {
-        if (W4_D * m < n) BOT[(W4_D * m + lane) & 63] = v;
-    };
+    auto bot_landed = [&]() { asm volatile("cp.async.wait_all;" ::: "memory"); };
     auto produce = [&](int64_t m) {
         const int rbm = (int)((W4_D * m) % W4_ROWS);
         switch (warp) {
@@ -317,18 +324,19 @@ __global__ void __launch_bounds__(256) k_gs1d_wave4(double* __restrict__ u, int6
         }
     };
 
-    // prologue: the previous block's first 48 positions, the partial sums of batch 0
-    double nextbot = c;
+    // prologue: the previous block's first 64 positions, the partial sums of batch 0
     if (warp == 7) {
-        bot_store(0, bot_fetch(0));
-        bot_store(1, bot_fetch(1));
-        nextbot = bot_fetch(2);
+        bot_fetch(0);
+        bot_fetch(1);
+        bot_landed();
+        bot_fetch(2);
     }
     __syncthreads();
     produce(0);
     __syncthreads();
 
-    double nw = c;  // chain: this lane's previous output (the left neighbour of its next point)
+    double nw = c;         // chain: this lane's previous output (the left neighbour of its next point)
+    int64_t pending = -1;  // warp 7: progress to publish at the start of the next batch
     for (int64_t m = 0; m <= mmax + 1; ++m) {
         if (warp == 0) {
             if (m <= mmax) {
@@ -338,25 +346,46 @@ __global__ void __launch_bounds__(256) k_gs1d_wave4(double* __restrict__ u, int6
                 for (int d = 0; d < W4_D; ++d) p[d] = Pb[m & 1][d][k];
                 const int row0 = (int)((W4_D * m) % W4_ROWS);
                 const int64_t x0 = W4_D * m - (int64_t)W4_S * k;
+                if (x0 >= 0 && x0 + W4_D <= n) {
+                    // the whole batch inside the grid: no predicate on the chain (lanes >= L compute
+                    // values nobody reads, so that the warp does not split between the two paths)
+                    // outputs kept in the registers of the sums they replace, stored after the chain
 #pragma unroll
-                for (int d = 0; d < W4_D; ++d) {
-                    const int64_t x = x0 + d;
-                    double o = c;
-                    if (k < L && x >= 0 && x < n) {
-                        o = acc_step<ARITH>(p[d], w.w[2], nw);
-                        nw = o;
+                    for (int d = 0; d < W4_D; ++d) {
+                        nw = acc_step<ARITH>(p[d], w.w[2], nw);
+                        p[d] = nw;
                     }
-                    O[row0 + d][k] = o;
+#pragma unroll
+                    for (int d = 0; d < W4_D; ++d) O[row0 + d][k] = p[d];
+                } else {
+#pragma unroll
+                    for (int d = 0; d < W4_D; ++d) {
+                        const int64_t x = x0 + d;
+                        double o = c;
+                        if (k < L && x >= 0 && x < n) {
+                            o = acc_step<ARITH>(p[d], w.w[2], nw);
+                            nw = o;
+                        }
+                        O[row0 + d][k] = o;
+                    }
                 }
             }
         } else if (warp < 7) {
             produce(m + 1);
         } else {
-            bot_store(m + 2, nextbot);  // read by batch m + 2's partial sums, next iteration
-            nextbot = bot_fetch(m + 3);
+            // progress for the final-sweep stores of earlier batches, first: the fence overlaps the chain
+            if (pending >= 0) {
+                if (lane == 0) {
+                    __threadfence();
+                    st_release64(mine, mytag | (unsigned long long)pending);
+                }
+                pending = -1;
+            }
+            bot_landed();      // batch m + 2's values (read next iteration) are in BOT
+            bot_fetch(m + 3);
             if (m >= 1 && m - 1 <= mmax) {
                 // the last lane's outputs of batch m - 1 (the block's final sweep) to the grid;
-                // this block's progress every 4 batches
+                // this block's progress every 4 batches, released at the start of the next batch
                 if (lane < W4_D) {
                     const int64_t j = W4_D * (m - 1) + lane, x = j - (int64_t)W4_S * (L - 1);
                     if (x >= 0 && x < n) u[x] = O[j % W4_ROWS][L - 1];
@@ -364,15 +393,13 @@ __global__ void __launch_bounds__(256) k_gs1d_wave4(double* __restrict__ u, int6
                 if ((m & 3) == 3 && publish) {
                     __syncwarp();
                     const int64_t xl = W4_D * (m - 1) + W4_D - 1 - (int64_t)W4_S * (L - 1);
-                    if (lane == 0 && xl >= 0) {
-                        __threadfence();
-                        st_release64(mine, mytag | (unsigned long long)(xl + 1 < n ? xl + 1 : n));
-                    }
+                    if (xl >= 0) pending = xl + 1 < n ? xl + 1 : n;
                 }
             }
         }
         __syncthreads();
     }
+    if (warp == 7) bot_landed();         // no copy into shared memory outlives the CTA
     if (threadIdx.x == 224 && publish) {  // warp 7, after its last stores
         __threadfence();
         st_release64(mine, mytag | (unsigned long long)n);
