@@ -122,7 +122,10 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
  * and grown when a run needs more; that first use must not be inside a
  * stream capture (EUNSUPPORTED there). T_b is lowered to fit the shortest
  * period (period >= 2 * T_b * r); an axis shorter than 2 * r points cannot be
- * tiled and returns EUNSUPPORTED.
+ * tiled and returns EUNSUPPORTED. In 1D, when every period fits on the GPU at
+ * once, the whole run is one cooperative launch in which each period advances
+ * its two segments together and exchanges edge values with its neighbours
+ * through flags (bounded waits: STENCIL_ETIMEOUT, never a hang).
  */
 int stencil_set_plan(stencil_handle h, int kernel, int tb, const int64_t tile[3]);
 

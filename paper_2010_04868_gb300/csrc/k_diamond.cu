@@ -491,8 +491,9 @@ __global__ void __launch_bounds__(256, (DIM == 2 && SHAPE == STAR && R == 1) ? 4
 // band into a shared ring of 8 levels as soon as it is published and a slot is
 // free, marking each level ready with a CTA-scope release; B's ring is written
 // from it HEX_LAG steps after the level, so the L2 round trips never sit on a
-// step. Every CTA must be resident at once (the launch checks the occupancy);
-// every wait is bounded and records STENCIL_ETIMEOUT instead of hanging.
+// step. Every CTA must be resident at once: the launch is cooperative (after an
+// occupancy check); every wait is bounded and records STENCIL_ETIMEOUT instead of
+// hanging.
 constexpr int HEX_LAG = 16;
 constexpr int SPIN_LIMIT_DIAMOND = 1 << 23;  // x ~0.25-0.5 us per poll: a wait gives up after two to four seconds
 
@@ -897,9 +898,24 @@ static int diamond_hex1d(const RunCtx& ctx, double* u, int64_t T, int H, const i
     WArr<2 * R + 1> w;
     for (int q = 0; q < 2 * R + 1; ++q) w.w[q] = h->w_desc[q];
     if (cudaMemsetAsync(h->dia_ws, 0, 2 * n * sizeof(int), ctx.st) != cudaSuccess) return STENCIL_ECUDA;
-    kern<<<(unsigned)n, nthr, smem, ctx.st>>>(u, G, w);
+    // a cooperative launch: every CTA waits on its neighbours, so all of them must be resident
+    // at once even when other streams' kernels share the GPU
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n);
+    cfg.blockDim = dim3(nthr);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx.st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, kern, u, G, w) != cudaSuccess) {
+        cudaGetLastError();
+        return STENCIL_EUNSUPPORTED;  // nothing but the flag reset enqueued: the phase launches run instead
+    }
     g_launches++;
-    return cuda_rc(cudaGetLastError());
+    return STENCIL_OK;
 }
 
 template <int DIM, int SHAPE, int R>
