@@ -30,10 +30,12 @@
 //     earlier phase's output (they differ in an axis where the earlier one is
 //     A and the later B), so no second grid is needed.
 // Inside a tile, levels run between two shared-memory buffers with one CTA
-// barrier per level; the ring of level k is fetched with cp.async while level
-// k is computed. Every point is computed once, with the same descending-order
-// sum and rounding as the plain kernel, so the result equals T plain steps
-// bit for bit.
+// barrier per level; the ring of level k is fetched with cp.async three levels
+// ahead, into frame positions that no level in between reads or writes. Every
+// point is computed once, with the same descending-order sum and rounding as
+// the plain kernel, so the result equals T plain steps bit for bit. In 1D,
+// when every period fits on the GPU at once, k_jacobi_hex1d below runs the
+// whole run in one launch instead.
 #include <algorithm>
 
 #include "internal.h"
