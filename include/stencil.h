@@ -107,7 +107,10 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
  *   tb       temporal block depth T_b (BLOCKED, DIAMOND) or sweeps per warp
  *            (WAVEFRONT, 1..32); 0 = default.
  *   tile     tile extents (slowest first) for BLOCKED; period lengths per axis
- *            (slowest first) for DIAMOND; 0 = default.
+ *            (slowest first) for DIAMOND; for WAVEFRONT in 2D/3D with a
+ *            constant boundary, tile[0] = CTAs per SM of the persistent
+ *            kernel and, in 2D with radius 1, tile[2] = points per lane and
+ *            step (8 or 16); 0 = default.
  * A family that cannot run a given (method, boundary, grid) makes stencil_run
  * return EUNSUPPORTED.
  *

@@ -933,9 +933,11 @@ static int launch_wave(const RunCtx& ctx, double* u, const WS& w, const WaveGeo&
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
-    // two CTAs (8 worker warps) per SM: more tiles in flight would slow the tiles on the DAG's
-    // critical path (they share the FP64 pipe); fewer leave it idle
-    int64_t nblk = (int64_t)nsm * (per_sm > 2 ? 2 : (per_sm > 0 ? per_sm : 1));
+    // two CTAs (8 worker warps) per SM by default: more tiles in flight would slow the tiles on
+    // the DAG's critical path (they share the FP64 pipe); fewer leave it idle. A fixed wavefront
+    // plan may ask for another count (tile[0]).
+    const int want = h->plan_kernel == STENCIL_KERNEL_WAVEFRONT && h->plan_tile[0] > 0 ? (int)h->plan_tile[0] : 2;
+    int64_t nblk = (int64_t)nsm * (per_sm > want ? want : (per_sm > 0 ? per_sm : 1));
     const int64_t need = (wg.ntiles + 3) / 4;
     if (nblk > need) nblk = need;
     const WaitCfg wc = take_wait_cfg(h);
@@ -1029,8 +1031,14 @@ static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, boo
         return STENCIL_EUNSUPPORTED;
     }
     if (h->dim == 2) {
-        if (h->shape == STAR && h->r == 1) return wave_tiles<2, STAR, 1, 16>(ctx, u, T, lanes, prep);
-        if (h->shape == BOX && h->r == 1) return wave_tiles<2, BOX, 1, 16>(ctx, u, T, lanes, prep);
+        // points per lane and step: 16, or 8 when a fixed wavefront plan asks for it (tile[2] = 8)
+        const bool w8 = h->plan_kernel == STENCIL_KERNEL_WAVEFRONT && h->plan_tile[2] == 8;
+        if (h->shape == STAR && h->r == 1)
+            return w8 ? wave_tiles<2, STAR, 1, 8>(ctx, u, T, lanes, prep)
+                      : wave_tiles<2, STAR, 1, 16>(ctx, u, T, lanes, prep);
+        if (h->shape == BOX && h->r == 1)
+            return w8 ? wave_tiles<2, BOX, 1, 8>(ctx, u, T, lanes, prep)
+                      : wave_tiles<2, BOX, 1, 16>(ctx, u, T, lanes, prep);
         if (h->shape == STAR && h->r == 2) return wave_tiles<2, STAR, 2, 8>(ctx, u, T, lanes, prep);
         if (h->shape == BOX && h->r == 2) return wave_tiles<2, BOX, 2, 8>(ctx, u, T, lanes, prep);
     } else {
