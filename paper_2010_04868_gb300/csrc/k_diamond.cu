@@ -699,7 +699,9 @@ __global__ void __launch_bounds__(512) k_jacobi_hex1d(double* __restrict__ u, He
                         progressed = true;
                     }
                 }
-                if (!progressed) {
+                if (progressed) {
+                    it = 0;  // the limit is on consecutive polls without progress
+                } else {
                     __nanosleep(64);
                     if (++it >= G.spin) {
                         ok = false;
