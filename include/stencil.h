@@ -226,11 +226,13 @@ int stencil_run_host(stencil_handle h, double* host_data, const int64_t ext[3], 
 uint64_t stencil_launch_count(void);
 
 /*
- * Failure-detection test hook (no counterpart in the paper). The next
- * wavefront Gauss-Seidel run of h never publishes the completion of one unit
- * of work: tile number `unit` in the 2D/3D kernel's schedule order, or sweep
- * block `unit` in 1D (-1 disables). Every wait on it gives up after `spin`
- * polls (0 = the default limit, about two seconds), the kernel finishes, and
+ * Failure-detection test hook (no counterpart in the paper). The next run of h
+ * that waits on other CTAs never publishes the completion of one unit of
+ * work: in the wavefront Gauss-Seidel kernels tile number `unit` in the 2D/3D
+ * schedule order, or sweep block `unit` in 1D; in the concurrent 1D diamond
+ * Jacobi kernel period `unit` (-1 disables). Every wait on it gives up after
+ * `spin` polls (0 = the default limit, about two seconds; in the diamond kernel
+ * the first wait that gives up ends the others at once), the kernel finishes, and
  * stencil_status() then returns STENCIL_ETIMEOUT. The grid's contents after
  * such a run are unspecified. Nothing faults, traps or hangs.
  */

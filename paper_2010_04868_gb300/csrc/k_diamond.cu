@@ -509,7 +509,9 @@ struct HexGeo {
     double* aband;       // n x H x 2r: left band of A per level of the current band
     double* btop;        // n x H r: the part of B's top right of the period
     int* status;
+    int* abort;          // grid-wide: set by the first wait that times out, so the others stop polling
     int spin;
+    int stall;           // failure-detection test hook: this period never publishes (-1: none)
 };
 
 __device__ __forceinline__ int hex_ld_acquire(const int* f)
@@ -519,12 +521,27 @@ __device__ __forceinline__ int hex_ld_acquire(const int* f)
     return x;
 }
 
-__device__ __forceinline__ bool hex_wait_ge(const int* f, int v, int spin)
+// A wait gave up: the CTA's other waits (*fail) and every other CTA's (*abort) stop polling.
+__device__ __forceinline__ void hex_give_up(volatile int* fail, int* abort)
 {
-    for (int it = 0; it < spin; ++it) {
+    *fail = 1;
+    *(volatile int*)abort = 1;
+}
+
+// True once another wait of this CTA or of the grid has given up.
+__device__ __forceinline__ bool hex_aborted(const volatile int* fail, const int* abort)
+{
+    return *fail || *(const volatile int*)abort;
+}
+
+// Bounded wait for *f >= v; gives up at once when another wait has timed out.
+__device__ __forceinline__ bool hex_wait_ge(const int* f, int v, int spin, volatile int* fail, int* abort)
+{
+    for (int it = 0; it < spin && !hex_aborted(fail, abort); ++it) {
         if (hex_ld_acquire(f) >= v) return true;
         __nanosleep(it < 64 ? 32 : 256);
     }
+    hex_give_up(fail, abort);
     return false;
 }
 
@@ -552,6 +569,7 @@ __global__ void __launch_bounds__(512) k_jacobi_hex1d(double* __restrict__ u, He
     extern __shared__ __align__(16) double sm[];
     __shared__ int step_done;   // compute warps: steps of the band completed
     __shared__ int ring_ready;  // comm warp: levels of the band in the ring
+    __shared__ int fail;        // a wait of this CTA timed out: every other wait gives up at once
     const int c = blockIdx.x, n = G.n, N = G.N;
     const int s0 = (int)((int64_t)c * N / n), s1 = (int)((int64_t)(c + 1) * N / n), P = s1 - s0;
     const int W = min(P, (P + 2 * G.H * R + 1) / 2);
@@ -575,7 +593,9 @@ __global__ void __launch_bounds__(512) k_jacobi_hex1d(double* __restrict__ u, He
     const int lane = tid - ncomp;
     const int cl = (c + n - 1) % n, cr = (c + 1) % n;
     const int seqH = G.H + 1;
-    bool ok = true;
+    const bool pub = c != G.stall;  // the failure-detection hook silences this period
+    volatile int* vfail = &fail;
+    if (tid == 0) fail = 0;
 
     // ---- the grid's values into buffer 0; cells outside the grid hold c in both buffers
     for (int i = tid; i < G.fwA; i += nthr) {
@@ -645,8 +665,8 @@ __global__ void __launch_bounds__(512) k_jacobi_hex1d(double* __restrict__ u, He
                         for (int it = 0; ring_known <= kr; ++it) {
                             ring_known = ld_acquire_cta(&ring_ready);
                             if (ring_known > kr) break;
-                            if (it >= G.spin) {
-                                ok = false;
+                            if (it >= G.spin || *vfail) {
+                                hex_give_up(vfail, G.abort);
                                 break;
                             }
                             __nanosleep(32);
@@ -675,7 +695,7 @@ __global__ void __launch_bounds__(512) k_jacobi_hex1d(double* __restrict__ u, He
                     for (int i = lane; i < (upto - rel) * 2 * R; i += 32)
                         G.aband[((int64_t)c * G.H + rel) * 2 * R + i] = alb[rel * 2 * R + i];
                     __syncwarp();
-                    if (lane == 0) hex_release(G.flagA + c, (int)b * seqH + upto);
+                    if (lane == 0 && pub) hex_release(G.flagA + c, (int)b * seqH + upto);
                     rel = upto;
                     progressed = true;
                 }
@@ -703,8 +723,8 @@ __global__ void __launch_bounds__(512) k_jacobi_hex1d(double* __restrict__ u, He
                     it = 0;  // the limit is on consecutive polls without progress
                 } else {
                     __nanosleep(64);
-                    if (++it >= G.spin) {
-                        ok = false;
+                    if (++it >= G.spin || ((it & 31) == 0 && hex_aborted(vfail, G.abort))) {
+                        hex_give_up(vfail, G.abort);
                         break;
                     }
                 }
@@ -719,8 +739,8 @@ __global__ void __launch_bounds__(512) k_jacobi_hex1d(double* __restrict__ u, He
         for (int i = tid; i < h * R; i += nthr) abase[loB - h * R + i - fA] = btop[loB - h * R + i - fB];
         __syncthreads();
         if (tid == 0) {
-            if (hasR) hex_release(G.flagB + c, (int)b + 1);
-            if (hasL && !hex_wait_ge(G.flagB + cl, (int)b + 1, G.spin)) ok = false;
+            if (hasR && pub) hex_release(G.flagB + c, (int)b + 1);
+            if (hasL) hex_wait_ge(G.flagB + cl, (int)b + 1, G.spin, vfail, G.abort);
         }
         __syncthreads();
         if (hasL)
@@ -732,7 +752,7 @@ __global__ void __launch_bounds__(512) k_jacobi_hex1d(double* __restrict__ u, He
     // ---- the period's final values back to the grid
     for (int i = loA + tid; i < hiA; i += nthr) u[i] = Ab(g0)[i - fA];
     for (int i = loB + tid; i < hiB; i += nthr) u[i] = Bb(g0)[i - fB];
-    if (!ok) atomicExch(G.status, DEV_TIMEOUT);
+    if (tid == 0 && *vfail) atomicExch(G.status, DEV_TIMEOUT);
 }
 
 // ------------------------------------------------------------------ host side
@@ -879,8 +899,8 @@ static int diamond_hex1d(const RunCtx& ctx, double* u, int64_t T, int H, const i
         return STENCIL_ECUDA;
     }
     if ((int64_t)per_sm * nsm < n) return STENCIL_EUNSUPPORTED;  // every CTA waits on its neighbours
-    // workspace: flags, A left bands, B top parts
-    const size_t flag_bytes = (size_t)((2 * n * sizeof(int) + 255) & ~size_t(255));
+    // workspace: flags (two per period and the abort word), A left bands, B top parts
+    const size_t flag_bytes = (size_t)(((2 * n + 1) * sizeof(int) + 255) & ~size_t(255));
     const size_t bytes = flag_bytes + (size_t)n * H * 3 * R * sizeof(double);
     int rc = diamond_workspace(const_cast<stencil_handle_s*>(h), bytes, ctx.st);
     if (rc) return rc;
@@ -895,13 +915,19 @@ static int diamond_hex1d(const RunCtx& ctx, double* u, int64_t T, int H, const i
     G.fwB = (int)fwB;
     G.flagA = (int*)h->dia_ws;
     G.flagB = G.flagA + n;
+    G.abort = G.flagA + 2 * n;
     G.aband = (double*)((char*)h->dia_ws + flag_bytes);
     G.btop = G.aband + (size_t)n * H * 2 * R;
     G.status = h->d_status;
-    G.spin = SPIN_LIMIT_DIAMOND;
+    // failure-detection test hook (stencil_debug_inject_stall): consumed by this run
+    stencil_handle_s* hm = const_cast<stencil_handle_s*>(h);
+    G.spin = hm->debug_spin > 0 ? hm->debug_spin : SPIN_LIMIT_DIAMOND;
+    G.stall = hm->debug_stall_tile >= 0 && hm->debug_stall_tile < n ? (int)hm->debug_stall_tile : -1;
+    hm->debug_stall_tile = -1;
+    hm->debug_spin = 0;
     WArr<2 * R + 1> w;
     for (int q = 0; q < 2 * R + 1; ++q) w.w[q] = h->w_desc[q];
-    if (cudaMemsetAsync(h->dia_ws, 0, 2 * n * sizeof(int), ctx.st) != cudaSuccess) return STENCIL_ECUDA;
+    if (cudaMemsetAsync(h->dia_ws, 0, (2 * n + 1) * sizeof(int), ctx.st) != cudaSuccess) return STENCIL_ECUDA;
     // a cooperative launch: every CTA waits on its neighbours, so all of them must be resident
     // at once even when other streams' kernels share the GPU
     cudaLaunchConfig_t cfg = {};

@@ -148,3 +148,25 @@ def test_diamond_run_replays_in_a_cuda_graph(dim, ext, H, periods):
         torch.cuda.synchronize()
         assert bits_equal(u.cpu().numpy(), ref)
     st.close()
+
+
+@pytest.mark.parametrize("bc,unit", [(0, 5), (0, 0), (1, 77)])
+def test_concurrent_1d_stalled_period_times_out_without_hanging(bc, unit):
+    """A period of the concurrent 1D kernel that never publishes its edges makes its neighbours'
+    bounded waits expire: the launch finishes, stencil_status() reports ETIMEOUT, and the next
+    run on the same handle is correct again."""
+    import torch
+    from paper_2010_04868_gb300 import stencil as S
+    w, u0 = case(1, "star", 2, (9000,), seed=41)
+    T = 90
+    st = S.Stencil(1, 0, 2, list(w), S.STENCIL_JACOBI, bc).set_plan(DIAMOND, 40, (0, 0, 0))
+    u = torch.from_numpy(u0.copy()).cuda()
+    S.stencil_debug_inject_stall(st.handle, unit, 20000)
+    st.run(u, T)
+    assert st.status() == S.STENCIL_ETIMEOUT
+    u.copy_(torch.from_numpy(u0))
+    st.run(u, T)
+    assert st.status() == 0
+    ref = oracle_run(u0, T, 1, "star", 2, w, "jacobi", "periodic" if bc else "constant", 0.0, "fma")
+    assert bits_equal(u.cpu().numpy(), ref), first_diff(u.cpu().numpy(), ref)
+    st.close()
