@@ -44,7 +44,7 @@ KERNEL_NAMES = {1: "plain", 2: "blocked", 3: "wavefront", 4: "diamond"}
 # per launch, algorithmically 16 B per point update (268.4 MB per launch).
 # Split (diamond) tiles: four launches (one per tile type) per band of T_b steps; the figure is the
 # band's total over four, so it includes the per-level edge bands the tiles exchange through L2/HBM.
-NCU_TRAFFIC = {("2d9p", "plain", 1, (0, 0, 0)): 134_247_168 + 94_438_912,
+NCU_TRAFFIC = {("2d9p", "plain", 1, (0, 0, 0)): 134_256_128 + 94_363_392,
                ("2d9p", "diamond", 16, (0, 88, 88)): (464_250_112 + 175_210_752) // 4}
 
 

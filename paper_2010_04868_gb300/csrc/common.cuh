@@ -147,6 +147,15 @@ __device__ __forceinline__ double fetch_bc(const double* u, int64_t i, int64_t j
     return u[(i * g.n1 + j) * g.n2 + k];
 }
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute (launch_pdl) may be scheduled while the
+// kernel before it in the stream is still draining its last CTAs, so that its
+// own launch latency overlaps that tail. griddepcontrol.wait then holds every
+// thread until the previous kernel has completed and its writes are visible;
+// such a kernel calls this before it touches memory the previous one may
+// write. Without a programmatic predecessor it returns at once.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Full update at (i, j, k) (inside the grid) with compile-time offsets and
 // the boundary rule applied to every term.
 template <int DIM, int SHAPE, int R, int ARITH, class WS>

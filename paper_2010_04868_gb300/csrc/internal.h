@@ -2,6 +2,7 @@
 #pragma once
 #include <atomic>
 #include <cstdint>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -53,6 +54,25 @@ struct RunCtx {
 };
 
 inline int cuda_rc(cudaError_t e) { return e == cudaSuccess ? STENCIL_OK : STENCIL_ECUDA; }
+
+// Launch with programmatic stream serialization (see griddep_wait): the kernel
+// must call griddep_wait() before its first access to memory that the kernel
+// before it in the stream may write.
+template <class... P, class... A>
+inline cudaError_t launch_pdl(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
 
 // Device-side description of h for a grid of npts points (the bound field, if any).
 inline StencilDev make_sd(const stencil_handle_s* h, int64_t npts)

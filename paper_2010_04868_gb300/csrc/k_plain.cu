@@ -65,17 +65,29 @@ __host__ __device__ constexpr int plain_rb()
                     : (DIM == 2 ? (FIELD ? PLAIN_FIELD_RB2 : (K <= 9 ? 4 : 2)) : (FIELD ? PLAIN_FIELD_RB3 : 2));
 }
 
-template <int DIM, bool FIELD>
+// Resident CTAs of 256 threads per SM the register budget must allow. The
+// interior path needs few registers but the boundary path in the same body
+// drove the allocation up (2D 72, 3D 7-point 80 with spills: 3 CTAs per SM);
+// capped at 64 (4 CTAs) they fit without spills, and the 4096^2 5-point step
+// runs ~6 % faster: 3 -> 4 resident CTAs of the same kernel shape measured
+// 93-96 -> 98-102 GStencil/s on one GB300. The 2D radius-2 star fits 3 CTAs
+// (78 registers, was 94: 2 CTAs); the 2D radius-2 box and the 27-point box
+// would spill under a tighter cap and keep the looser one.
+template <int DIM, int SHAPE, int R, bool FIELD>
 __host__ __device__ constexpr int plain_minb()
 {
-    return DIM == 3 ? (FIELD ? PLAIN_FIELD_MINB3 : 3) : (FIELD ? PLAIN_FIELD_MINB2 : 1);
+    if (FIELD) return DIM == 3 ? PLAIN_FIELD_MINB3 : (DIM == 2 ? PLAIN_FIELD_MINB2 : 1);
+    if (DIM == 2) return R == 1 ? 4 : (SHAPE == STAR ? 3 : 1);
+    if (DIM == 3) return SHAPE == STAR && R == 1 ? 4 : 3;
+    return 1;
 }
 
 template <int DIM, int SHAPE, int R, int ARITH, class WS>
-__global__ void __launch_bounds__(256, plain_minb<DIM, WS::per_point>()) k_jacobi_plain(const double* __restrict__ u,
+__global__ void __launch_bounds__(256, plain_minb<DIM, SHAPE, R, WS::per_point>()) k_jacobi_plain(const double* __restrict__ u,
                                                       double* __restrict__ v, Geo g, int bc, double c, WS w)
 {
     constexpr int RB = plain_rb<DIM, Stn<DIM, SHAPE, R>::K, WS::per_point>();
+    griddep_wait();  // launched programmatically: the previous step's writes are visible after this
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n2) return;
     const int64_t s1 = g.n2, s0 = g.n1 * g.n2;
@@ -150,10 +162,13 @@ static void launch_jacobi_plain(const RunCtx& ctx, const double* in, double* out
         const int64_t gy = (ctx.g.n1 + (int64_t)block.y * RB - 1) / ((int64_t)block.y * RB);
         grid.y = (unsigned)(gy < 65535 ? gy : 65535);
     }
-    if (ctx.h->arith == ARITH_FMA)
-        k_jacobi_plain<DIM, SHAPE, R, ARITH_FMA, WS><<<grid, block, 0, ctx.st>>>(in, out, ctx.g, ctx.h->bc, ctx.h->c, w);
-    else
-        k_jacobi_plain<DIM, SHAPE, R, ARITH_UNFUSED, WS><<<grid, block, 0, ctx.st>>>(in, out, ctx.g, ctx.h->bc, ctx.h->c, w);
+    // programmatic launch: the next step's CTAs are scheduled while this one drains (+1-2 %)
+    auto kern = ctx.h->arith == ARITH_FMA ? k_jacobi_plain<DIM, SHAPE, R, ARITH_FMA, WS>
+                                          : k_jacobi_plain<DIM, SHAPE, R, ARITH_UNFUSED, WS>;
+    if (launch_pdl(kern, grid, block, 0, ctx.st, in, out, ctx.g, ctx.h->bc, ctx.h->c, w) != cudaSuccess) {
+        cudaGetLastError();  // a stream that refuses the attribute: an ordinary launch
+        kern<<<grid, block, 0, ctx.st>>>(in, out, ctx.g, ctx.h->bc, ctx.h->c, w);
+    }
 }
 
 template <int DIM, int SHAPE, int R>
