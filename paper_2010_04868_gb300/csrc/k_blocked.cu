@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(256) k_jacobi_blocked(const __grid_constant__ 
     const int64_t g2 = (DIM >= 1 && b.use_tma) ? (x2 >= 0 ? (x2 & ~int64_t(1)) : -((-x2 + 1) & ~int64_t(1))) : x2;
     const int pad2 = (int)(x2 - g2);  // 0 or 1
     const int nthr = blockDim.x;
+    griddep_wait();  // launched programmatically: the previous pass has finished with both buffers
 
     // ---- stage tile + halo
     if (b.use_tma) {
@@ -327,8 +328,13 @@ static int blocked_passes(const RunCtx& ctx, double* a, double* bb, int64_t T, i
     double* dst = bb;
     for (int64_t done = 0; done < T;) {
         b.tb = (int)((T - done) < full_tb ? (T - done) : full_tb);
-        kern<<<nblk, 256, smem, ctx.st>>>(src == a ? mapA : mapB, src, dst, ctx.g, ctx.h->bc, ctx.h->c, b, w,
-                                          ctx.h->d_status);
+        // programmatic launch: the next pass's CTAs are scheduled while this one drains
+        const CUtensorMap& map = src == a ? mapA : mapB;
+        if (launch_pdl(kern, dim3(nblk), dim3(256), smem, ctx.st, map, src, dst, ctx.g, ctx.h->bc, ctx.h->c, b, w,
+                       ctx.h->d_status) != cudaSuccess) {
+            cudaGetLastError();  // a stream that refuses the attribute: an ordinary launch
+            kern<<<nblk, 256, smem, ctx.st>>>(map, src, dst, ctx.g, ctx.h->bc, ctx.h->c, b, w, ctx.h->d_status);
+        }
         g_launches++;
         if (cudaGetLastError() != cudaSuccess) return STENCIL_ECUDA;
         done += b.tb;
