@@ -109,8 +109,9 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
  *   tile     tile extents (slowest first) for BLOCKED; period lengths per axis
  *            (slowest first) for DIAMOND; for WAVEFRONT in 2D/3D with a
  *            constant boundary, tile[0] = CTAs per SM of the persistent
- *            kernel and, in 2D with radius 1, tile[2] = points per lane and
- *            step (8 or 16); 0 = default.
+ *            kernel, in 2D tile[1] = skewed rows per tile (2..64) and, in 2D
+ *            with radius 1, tile[2] = points per lane and step (8 or 16);
+ *            0 = default.
  * A family that cannot run a given (method, boundary, grid) makes stencil_run
  * return EUNSUPPORTED.
  *

@@ -860,7 +860,9 @@ static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes, bool p
         wg.a1 = box ? R : 0;
         wg.b1 = R * (1 + wg.a1);
         wg.a2 = wg.c2 = wg.b2 = 0;
-        wg.H = 16;
+        // skewed rows per tile: 16, or what a fixed wavefront plan asks for (tile[1], 2..64)
+        const int64_t hp = h->plan_kernel == STENCIL_KERNEL_WAVEFRONT ? h->plan_tile[1] : 0;
+        wg.H = hp >= 2 && hp <= 64 ? (int)hp : 16;
         wg.HJ = 1;
     } else {
         wg.a1 = box ? R : 0;

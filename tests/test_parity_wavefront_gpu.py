@@ -130,9 +130,10 @@ def test_periodic_box_wavefront_is_rejected():
 
 
 @pytest.mark.parametrize("shape,ext", [("star", (130, 77)), ("box", (70, 131))])
-@pytest.mark.parametrize("tile", [(0, 0, 8), (4, 0, 8), (3, 0, 16)])
+@pytest.mark.parametrize("tile", [(0, 0, 8), (4, 0, 8), (3, 0, 16), (0, 2, 0), (2, 5, 8), (3, 8, 16), (0, 64, 16)])
 def test_gs2d_wavefront_plan_parameters(shape, ext, tile):
-    """Points per lane and step (8 or 16) and CTAs per SM of the 2D wavefront change nothing in the result."""
+    """Points per lane and step (8 or 16), skewed rows per tile and CTAs per SM of the 2D wavefront change
+    nothing in the result."""
     w, u0 = case(2, shape, 1, ext, seed=99)
     for T in (1, 33, 70):
         ref = oracle_run(u0, T, 2, shape, 1, w, "gs", "constant", 0.3, "fma")
