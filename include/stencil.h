@@ -110,8 +110,10 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
  *            (slowest first) for DIAMOND; for WAVEFRONT in 2D/3D with a
  *            constant boundary, tile[0] = CTAs per SM of the persistent
  *            kernel, in 2D tile[1] = skewed rows per tile (2..64) and, in 2D
- *            with radius 1, tile[2] = points per lane and step (8 or 16);
- *            0 = default.
+ *            with radius 1, tile[2] = points per lane and step of the
+ *            one-warp tile (8 or 16; for the 5-point star with one weight
+ *            per term, 0 selects the decoupled tile: a chain warp, producer
+ *            warps and a scheduler warp per tile); 0 = default.
  * A family that cannot run a given (method, boundary, grid) makes stencil_run
  * return EUNSUPPORTED.
  *

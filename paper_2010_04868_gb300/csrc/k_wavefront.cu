@@ -600,6 +600,171 @@ __global__ void __launch_bounds__(128) k_gs_wave(double* __restrict__ u, Geo g, 
     }
 }
 
+// 2D 5-point star (radius 1), constant boundary, one weight per term: the
+// decoupled tile. In the one-warp tile above a lane-step of 16 points is 80
+// FP64 instructions, and a warp issues at most one per ~64 clocks, so a tile
+// on the DAG's critical path takes ~5100 clocks per step even when it has
+// the SM's FP64 pipe to itself. Here a CTA works on one tile at a time and
+// splits each point's sum, in the same descending order and rounding:
+//   producer warps (GD_NP, a share of the 16 points each) form
+//     P = w(+1,0) u'(i+1,j) (+) w(0,+1) u'(i,j+1) (+) w(0,0) u'(i,j)
+//   from the previous sweep's values for the NEXT step of every lane;
+//   the chain warp does u(i,j) = (P (+) w(0,-1) u(i,j-1)) (+) w(-1,0) u(i-1,j),
+//   the two newest-value terms, 32 dependent instructions per step;
+//   the scheduler warp takes the next tile's ticket, finds the tile and
+//   waits for its predecessors while the current tile computes.
+// Lanes are GD_S = 3 rows apart (one more than the one-warp tile), so the
+// previous-sweep values a producer reads for step st + 1 were written by
+// lane k - 1 at steps st - 2 and st - 1, and none of them is overwritten
+// before step st + 1: one barrier per step orders the two roles. The newest
+// value left of a lane's first point (tile J - 1) and the row above its
+// first step (tile I - 1) come from finished tiles; the row above every
+// later step is the chain's own output of the step before, kept in registers.
+constexpr int GD_W = 16;  // points per lane and step
+constexpr int GD_S = 3;   // rows between consecutive lanes (sweeps)
+constexpr int GD_NP = 4;  // producer warps
+constexpr int GD_THREADS = 32 * (GD_NP + 2);
+
+template <int ARITH, int M0, int M1>
+__device__ __forceinline__ void gd_produce(const double* __restrict__ u, const Geo& g, double c, const WArr<5>& w,
+                                           int64_t q, int64_t p2, double* __restrict__ P)
+{
+    const int64_t rq = q * g.n2;
+    double below[M1 - M0], right[M1 - M0], centre[M1 - M0];
+#pragma unroll
+    for (int m = M0; m < M1; ++m) {
+        const int64_t col = p2 + m;
+        const bool in = col >= 0 && col < g.n2;
+        below[m - M0] = in && q + 1 < g.n1 ? __ldcg(u + rq + g.n2 + col) : c;
+        right[m - M0] = in && col + 1 < g.n2 ? __ldcg(u + rq + col + 1) : c;
+        centre[m - M0] = in ? __ldcg(u + rq + col) : c;
+    }
+#pragma unroll
+    for (int m = M0; m < M1; ++m) {
+        double acc = __dmul_rn(w.w[0], below[m - M0]);
+        acc = acc_step<ARITH>(acc, w.w[1], right[m - M0]);
+        P[m] = acc_step<ARITH>(acc, w.w[2], centre[m - M0]);
+    }
+}
+
+template <int ARITH>
+__global__ void __launch_bounds__(GD_THREADS) k_gs2d_dec(double* __restrict__ u, Geo g, double c, WArr<5> w,
+                                                         WaveGeo wg, const int64_t* __restrict__ pre,
+                                                         int* __restrict__ flags, int* __restrict__ ticket,
+                                                         int* status, int tag, WaitCfg wc)
+{
+    __shared__ double Ps[2][32][GD_W + 1];  // P of a step, per lane (padded: conflict-free lane-strided reads)
+    __shared__ double L0s[2][32];           // newest value left of the lane's first point, per step
+    __shared__ double A0s[32][GD_W + 1];    // newest row above the tile's first step
+    __shared__ long long nxt[4];            // the next tile: ticket, b, I, J
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int NCOMP = 32 * (GD_NP + 1);  // chain + producers: the per-step barrier
+    constexpr int SCHED = GD_NP + 1;
+    bool ok = true;
+
+    // scheduler: the next tile's ticket and coordinates; returns once its predecessors are done
+    auto fetch = [&]() {
+        if (lane == 0) {
+            const int64_t tk = (int64_t)atomicAdd((unsigned long long*)ticket, 1ull);
+            int64_t b = 0, I = 0, J = 0, K = 0;
+            if (tk < wg.ntiles) {
+                decode_tile<2>(tk, pre, wg, b, I, J, K);
+                const int64_t fidx = (b * wg.nI + I) * wg.nJ + J;
+                if (I > 0) ok &= wait_flag(flags + fidx - wg.nJ, tag, wc.spin);
+                if (J > 0) ok &= wait_flag(flags + fidx - 1, tag, wc.spin);
+                if (b > 0) {
+                    const int64_t pI = I + wg.dI < wg.nI - 1 ? I + wg.dI : wg.nI - 1;
+                    const int64_t pJ = J + wg.dJ < wg.nJ - 1 ? J + wg.dJ : wg.nJ - 1;
+                    ok &= wait_flag(flags + ((b - 1) * wg.nI + pI) * wg.nJ + pJ, tag, wc.spin);
+                }
+            }
+            nxt[0] = tk;
+            nxt[1] = b;
+            nxt[2] = I;
+            nxt[3] = J;
+        }
+        __syncwarp();
+    };
+
+    if (warp == SCHED) fetch();
+    __syncthreads();
+    for (;;) {
+        const int64_t tk = nxt[0], b = nxt[1], I = nxt[2], J = nxt[3];
+        __syncthreads();  // every warp has the tile before the scheduler overwrites nxt
+        if (tk >= wg.ntiles) break;
+        if (warp == SCHED) {
+            fetch();
+        } else {
+            const int64_t L = wg.T - 32 * b < 32 ? wg.T - 32 * b : 32;
+            const bool lact = lane < L;
+            const int64_t p2 = J * GD_W - (int64_t)wg.b1 * lane;  // a1 = 0: the same columns at every step
+            const int64_t r0 = I * wg.H - (int64_t)GD_S * lane;   // the lane's row at step 0
+            // producers: P of step sn for every lane into slot sn & 1 (and the newest left value;
+            // at sn = 0 also the row above)
+            auto produce = [&](int sn) {
+                const int64_t q = r0 + sn;
+                if (!lact || q < 0 || q >= g.n1) return;
+                double* P = Ps[sn & 1][lane];
+                switch (warp) {
+                    case 1: gd_produce<ARITH, 0, 4>(u, g, c, w, q, p2, P); break;
+                    case 2: gd_produce<ARITH, 4, 8>(u, g, c, w, q, p2, P); break;
+                    case 3: gd_produce<ARITH, 8, 12>(u, g, c, w, q, p2, P); break;
+                    default: gd_produce<ARITH, 12, 16>(u, g, c, w, q, p2, P); break;
+                }
+                if (warp == 1)
+                    L0s[sn & 1][lane] = p2 - 1 >= 0 && p2 - 1 < g.n2 ? __ldcg(u + q * g.n2 + p2 - 1) : c;
+                if (sn == 0) {
+                    const int m0 = (warp - 1) * 4;
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        const int64_t col = p2 + m0 + d;
+                        A0s[lane][m0 + d] = q >= 1 && col >= 0 && col < g.n2 ? __ldcg(u + (q - 1) * g.n2 + col) : c;
+                    }
+                }
+            };
+            if (warp >= 1) produce(0);
+            asm volatile("bar.sync 1, %0;" ::"r"(NCOMP) : "memory");
+            double above[GD_W];
+#pragma unroll
+            for (int m = 0; m < GD_W; ++m) above[m] = c;
+            for (int st = 0; st < wg.H; ++st) {
+                if (warp == 0) {
+                    const int64_t q = r0 + st;
+                    if (lact && q >= 0 && q < g.n1) {
+                        const double* P = Ps[st & 1][lane];
+                        double left = L0s[st & 1][lane];
+                        double* row = u + q * g.n2;
+#pragma unroll
+                        for (int m = 0; m < GD_W; ++m) {
+                            const int64_t col = p2 + m;
+                            if (col >= 0 && col < g.n2) {
+                                const double a = st == 0 ? A0s[lane][m] : (q == 0 ? c : above[m]);
+                                const double t = acc_step<ARITH>(P[m], w.w[3], left);
+                                const double o = acc_step<ARITH>(t, w.w[4], a);
+                                row[col] = o;
+                                left = o;
+                                above[m] = o;
+                            } else {
+                                left = c;
+                            }
+                        }
+                    }
+                } else if (st + 1 < wg.H) {
+                    produce(st + 1);
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(NCOMP) : "memory");
+            }
+            const int64_t fidx = (b * wg.nI + I) * wg.nJ + J;
+            if (tid == 0 && fidx != wc.stall) {
+                __threadfence();
+                st_release(flags + fidx, tag);
+            }
+        }
+        __syncthreads();
+    }
+    if (warp == SCHED && lane == 0 && !ok) atomicExch(status, DEV_TIMEOUT);
+}
+
 // Schedule table: pre[d] = number of tiles on diagonals before d (tiles on
 // diagonal d: b*db + I + J + K = d). Counts in parallel, prefix sum by one thread.
 template <int DIM>
@@ -847,15 +1012,20 @@ template <int DIM, int SHAPE, int R, class WS>
 static int launch_sweepdag(const RunCtx& ctx, double* u, const WS& w, const SweepDag& t, const int64_t* dpre,
                            int* flags, unsigned long long* ctr);
 
+template <int ARITH>
+static int launch_gs2d_dec(const RunCtx& ctx, double* u, const WaveGeo& wg, const int64_t* dpre, int* flags,
+                           int* ticket, int tag);
+
+// dec: the decoupled tile (k_gs2d_dec; 2D 5-point star with one weight per term only)
 template <int DIM, int SHAPE, int R, int W>
-static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes, bool prepare_only = false)
+static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes, bool prepare_only = false, bool dec = false)
 {
     (void)lanes;
     stencil_handle_s* h = ctx.h;
     const Geo& g = ctx.g;
     const bool box = SHAPE == BOX;
     WaveGeo wg;
-    wg.s = R + 1;
+    wg.s = dec ? GD_S : R + 1;
     if (DIM == 2) {
         wg.a1 = box ? R : 0;
         wg.b1 = R * (1 + wg.a1);
@@ -916,6 +1086,11 @@ static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes, bool p
     if (cudaMemsetAsync(flags, 0, (size_t)wg.ntiles * sizeof(int), ctx.st) != cudaSuccess) return STENCIL_ECUDA;
     k_wave_prefix<DIM><<<1, 256, 0, ctx.st>>>(wg, dpre);
     g_launches++;
+    if constexpr (DIM == 2 && SHAPE == STAR && R == 1 && W == GD_W) {
+        if (dec)
+            return h->arith == ARITH_FMA ? launch_gs2d_dec<ARITH_FMA>(ctx, u, wg, dpre, flags, ticket, tag)
+                                         : launch_gs2d_dec<ARITH_UNFUSED>(ctx, u, wg, dpre, flags, ticket, tag);
+    }
     constexpr int K = Stn<DIM, SHAPE, R>::K;
     if (ctx.sd.field)
         return launch_wave<DIM, SHAPE, R, W>(ctx, u, WField<K>{ctx.sd.field, ctx.sd.npts}, wg, dpre, flags, ticket, tag);
@@ -944,6 +1119,32 @@ static int launch_wave(const RunCtx& ctx, double* u, const WS& w, const WaveGeo&
     if (nblk > need) nblk = need;
     const WaitCfg wc = take_wait_cfg(h);
     kern<<<(unsigned)nblk, 128, 0, ctx.st>>>(u, ctx.g, h->c, w, wg, dpre, flags, ticket, h->d_status, tag, wc);
+    g_launches++;
+    return cuda_rc(cudaGetLastError());
+}
+
+template <int ARITH>
+static int launch_gs2d_dec(const RunCtx& ctx, double* u, const WaveGeo& wg, const int64_t* dpre, int* flags,
+                           int* ticket, int tag)
+{
+    stencil_handle_s* h = ctx.h;
+    WArr<5> w;
+    for (int q = 0; q < 5; ++q) w.w[q] = h->w_desc[q];
+    auto kern = k_gs2d_dec<ARITH>;
+    int nsm = 0, per_sm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GD_THREADS, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return STENCIL_ECUDA;
+    }
+    // every CTA waits on tiles other CTAs hold: all of them must be resident (the count is capped
+    // at the occupancy); 2 per SM by default, or what a fixed wavefront plan asks for (tile[0])
+    const int want = h->plan_kernel == STENCIL_KERNEL_WAVEFRONT && h->plan_tile[0] > 0 ? (int)h->plan_tile[0] : 2;
+    int64_t nblk = (int64_t)nsm * (per_sm < want ? per_sm : want);
+    if (nblk > wg.ntiles) nblk = wg.ntiles;
+    const WaitCfg wc = take_wait_cfg(h);
+    kern<<<(unsigned)nblk, GD_THREADS, 0, ctx.st>>>(u, ctx.g, h->c, w, wg, dpre, flags, ticket, h->d_status, tag, wc);
     g_launches++;
     return cuda_rc(cudaGetLastError());
 }
@@ -1033,11 +1234,14 @@ static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, boo
         return STENCIL_EUNSUPPORTED;
     }
     if (h->dim == 2) {
-        // points per lane and step: 16, or 8 when a fixed wavefront plan asks for it (tile[2] = 8)
-        const bool w8 = h->plan_kernel == STENCIL_KERNEL_WAVEFRONT && h->plan_tile[2] == 8;
+        // points per lane and step: 16, or 8 when a fixed wavefront plan asks for it (tile[2] = 8);
+        // the 5-point star with one weight per term runs the decoupled tile unless the plan asks
+        // for the one-warp tile (tile[2] = 8 or 16)
+        const int64_t pw = h->plan_kernel == STENCIL_KERNEL_WAVEFRONT ? h->plan_tile[2] : 0;
+        const bool w8 = pw == 8;
         if (h->shape == STAR && h->r == 1)
             return w8 ? wave_tiles<2, STAR, 1, 8>(ctx, u, T, lanes, prep)
-                      : wave_tiles<2, STAR, 1, 16>(ctx, u, T, lanes, prep);
+                      : wave_tiles<2, STAR, 1, 16>(ctx, u, T, lanes, prep, pw == 0 && !ctx.sd.field);
         if (h->shape == BOX && h->r == 1)
             return w8 ? wave_tiles<2, BOX, 1, 8>(ctx, u, T, lanes, prep)
                       : wave_tiles<2, BOX, 1, 16>(ctx, u, T, lanes, prep);

@@ -7,10 +7,15 @@ barrier per step) and the communication warp (releases this CTA's A levels,
 acquires the next period's, fills a ring of 8 levels); the CTA barriers at band
 ends join them. k_gs1d_wave4 (Gauss-Seidel sweeps on warp lanes, skew 33, one
 chain warp and six partial-sum warps per 16-step batch): the warps' tasks of a
-batch run in random order between barriers. Random interleavings of all
-coroutines must neither deadlock nor read a value before it is published (every
-value carries its band/level or step), and both must give the oracle's grid
-bit for bit (unfused rounding).
+batch run in random order between barriers. k_gs2d_dec (2D 5-point
+Gauss-Seidel, sweeps on warp lanes 3 rows apart, tiles of a DAG; per step the
+chain warp's two newest-value terms and the producer warps' three
+previous-sweep terms of the next step): tiles in random orders that respect
+the DAG, the two roles of a step in either order, and every cell read checked
+for the sweep its value must carry. Random interleavings of all coroutines
+must neither deadlock nor read a value before it is published (every value
+carries its band/level or step), and all must give the oracle's grid bit for
+bit (unfused rounding).
 """
 import random
 
@@ -290,3 +295,101 @@ def test_gauss_seidel_1d_wavefront_schedule(N, T, c):
     ref = oracle_run(u0, T, 1, "star", 1, w, "gs", "constant", c, "unfused")
     for seed in (1, 2):
         assert bits_equal(run_gs1d_wave(u0, T, w, c, seed), ref), seed
+
+
+def run_gs2d_dec(u0, T, w, cval, seed, H=16, W=16, S=3):
+    """The decoupled 2D tile's schedule: lane k of sweep block b applies sweep 32 b + k + 1 at rows
+    r0 + st (r0 = I H - S k) and columns p2 .. p2 + W - 1 (p2 = J W - k); the producers form the three
+    previous-sweep terms of step st + 1 while the chain applies the two newest-value terms of step st."""
+    n1, n2 = u0.shape
+    u, ver = u0.copy(), np.zeros(u0.shape, dtype=np.int64)  # ver: sweeps applied to each cell
+    wd, rng = list(reversed(w)), random.Random(seed)  # (+1,0), (0,+1), (0,0), (0,-1), (-1,0)
+    R, L32, b1 = 1, 32, 1
+    nI = -(-(n1 + S * (L32 - 1)) // H)
+    nJ = -(-(n2 + b1 * (L32 - 1)) // W)
+    nB = -(-T // 32)
+    dI, dJ = (R + S * (L32 - 1)) // H + 2, (R + b1 * (L32 - 1)) // W + 2
+
+    def deps(b, I, J):
+        d = []
+        if I > 0:
+            d.append((b, I - 1, J))
+        if J > 0:
+            d.append((b, I, J - 1))
+        if b > 0:
+            d.append((b - 1, min(I + dI, nI - 1), min(J + dJ, nJ - 1)))
+        return d
+
+    def rd(q, col, sweeps):
+        if not (0 <= q < n1 and 0 <= col < n2):
+            return cval
+        assert ver[q, col] == sweeps, ("cell read with the wrong sweep", q, col, ver[q, col], sweeps)
+        return u[q, col]
+
+    def tile(b, I, J):
+        Lb = min(32, T - 32 * b)
+        P, L0, A0 = [dict(), dict()], [dict(), dict()], {}
+        above = [[cval] * W for _ in range(32)]
+
+        def produce(sn):
+            for k in range(Lb):
+                q, p2, sw = I * H - S * k + sn, J * W - b1 * k, 32 * b + k
+                if not 0 <= q < n1:
+                    continue
+                for m in range(W):
+                    col = p2 + m
+                    if 0 <= col < n2:
+                        acc = wd[0] * rd(q + 1, col, sw)
+                        acc = acc + wd[1] * rd(q, col + 1, sw)
+                        P[sn & 1][(k, m)] = (acc + wd[2] * rd(q, col, sw), sn)
+                    if sn == 0:
+                        A0[(k, m)] = rd(q - 1, col, sw + 1) if q >= 1 and 0 <= col < n2 else cval
+                L0[sn & 1][k] = (rd(q, p2 - 1, sw + 1), sn)
+
+        def chain(st):
+            for k in range(Lb):
+                q, p2, sw = I * H - S * k + st, J * W - b1 * k, 32 * b + k
+                if not 0 <= q < n1:
+                    continue
+                left, s0 = L0[st & 1][k]
+                assert s0 == st, "newest left value stale"
+                for m in range(W):
+                    col = p2 + m
+                    if 0 <= col < n2:
+                        a = A0[(k, m)] if st == 0 else (cval if q == 0 else above[k][m])
+                        p, sp = P[st & 1][(k, m)]
+                        assert sp == st, "partial sum stale"
+                        o = (p + wd[3] * left) + wd[4] * a
+                        assert ver[q, col] == sw, "overwrites a value of the wrong sweep"
+                        u[q, col], ver[q, col] = o, sw + 1
+                        left = above[k][m] = o
+                    else:
+                        left = cval
+
+        produce(0)
+        for st in range(H):
+            tasks = [lambda: chain(st)] + ([lambda: produce(st + 1)] if st + 1 < H else [])
+            rng.shuffle(tasks)  # the chain and the producers of a step run concurrently
+            for f in tasks:
+                f()
+
+    done, pending = set(), [(b, I, J) for b in range(nB) for I in range(nI) for J in range(nJ)]
+    while pending:  # any order that respects the DAG
+        ready = [t for t in pending if all(d in done for d in deps(*t))]
+        assert ready, "the tile DAG deadlocks"
+        t = ready[rng.randrange(len(ready))] if rng.random() < 0.7 else min(ready, key=lambda x: x[0] * 10 ** 6 +
+                                                                                   (x[1] + x[2]))
+        pending.remove(t)
+        tile(*t)
+        done.add(t)
+    return u
+
+
+@pytest.mark.parametrize("ext,T,c,H", [((20, 24), 40, 0.0, 16), ((37, 50), 70, 0.4, 16), ((9, 40), 33, 0.0, 4),
+                                       ((1, 1), 3, 0.7, 16), ((40, 7), 35, 0.0, 8)])
+def test_gauss_seidel_2d_decoupled_tile_schedule(ext, T, c, H):
+    w = list(inputs.normalized_weights(ext[0] * 7 + T, 5))
+    u0 = inputs.grid(ext[1] * 5 + T, ext)
+    ref = oracle_run(u0, T, 2, "star", 1, w, "gs", "constant", c, "unfused")
+    for seed in (1, 2):
+        assert bits_equal(run_gs2d_dec(u0, T, w, c, seed, H=H), ref), seed
