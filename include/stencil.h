@@ -111,8 +111,8 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
  *            constant boundary, tile[0] = CTAs per SM of the persistent
  *            kernel, in 2D tile[1] = skewed rows per tile (2..64) and, in 2D
  *            with radius 1, tile[2] = points per lane and step of the
- *            one-warp tile (8 or 16; for the 5-point star with one weight
- *            per term, 0 selects the decoupled tile: a chain warp, producer
+ *            one-warp tile (8 or 16), or 1 for the decoupled tile of the
+ *            5-point star with one weight per term (a chain warp, producer
  *            warps and a scheduler warp per tile); 0 = default.
  * A family that cannot run a given (method, boundary, grid) makes stencil_run
  * return EUNSUPPORTED.

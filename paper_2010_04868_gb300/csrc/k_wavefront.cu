@@ -613,89 +613,37 @@ __global__ void __launch_bounds__(128) k_gs_wave(double* __restrict__ u, Geo g, 
 //   the two newest-value terms, 32 dependent instructions per step;
 //   the scheduler warp takes the next tile's ticket, finds the tile and
 //   waits for its predecessors while the current tile computes.
-// Lanes are GD_S = 4 rows apart (two more than the one-warp tile), so the
-// previous-sweep values of step st + 2 (lane k - 1's outputs of steps st - 2
-// and st - 1) exist during step st: the producers load them then, into
-// registers, and combine them in step st + 1, so that the L2 latency of the
-// loads overlaps a chain step; no cell they read is overwritten before the
-// load (lane k writes those rows at steps st + 2 and st + 3). One barrier per
-// step orders the two roles. The newest value left of a lane's first point
-// (tile J - 1) and the row above its first step (tile I - 1) come from
-// finished tiles; the row above every later step is the chain's own output of
-// the step before, kept in registers.
+// Lanes are GD_S = 3 rows apart (one more than the one-warp tile), so the
+// previous-sweep values a producer reads for step st + 1 were written by
+// lane k - 1 at steps st - 2 and st - 1, and none of them is overwritten
+// before step st + 1: one barrier per step orders the two roles. The newest
+// value left of a lane's first point (tile J - 1) and the row above its
+// first step (tile I - 1) come from finished tiles; the row above every
+// later step is the chain's own output of the step before, kept in registers.
 constexpr int GD_W = 16;  // points per lane and step
-constexpr int GD_S = 4;   // rows between consecutive lanes (sweeps)
-constexpr int GD_NP = 4;  // producer warps (GD_W / GD_NP points each)
+constexpr int GD_S = 3;   // rows between consecutive lanes (sweeps)
+constexpr int GD_NP = 4;  // producer warps
 constexpr int GD_THREADS = 32 * (GD_NP + 2);
 
-// A producer's previous-sweep values of one step (GD_PW points of its lane from column p) and the
-// newest value left of the lane's first point.
-constexpr int GD_PW = GD_W / GD_NP;  // points per producer warp
-struct GdWin {
-    double below[GD_PW], right[GD_PW], centre[GD_PW], left;
-};
-
-// Loads for row q (inside the grid), columns p .. p + GD_PW - 1; cells outside the grid read c.
-// first: also the newest value left of the lane's first point (column p2 - 1).
-__device__ __forceinline__ void gd_load(const double* __restrict__ u, const Geo& g, double c, int64_t q, int64_t p,
-                                        int64_t p2, bool first, GdWin& V)
+template <int ARITH, int M0, int M1>
+__device__ __forceinline__ void gd_produce(const double* __restrict__ u, const Geo& g, double c, const WArr<5>& w,
+                                           int64_t q, int64_t p2, double* __restrict__ P)
 {
     const int64_t rq = q * g.n2;
+    double below[M1 - M0], right[M1 - M0], centre[M1 - M0];
 #pragma unroll
-    for (int d = 0; d < GD_PW; ++d) {
-        const int64_t col = p + d;
+    for (int m = M0; m < M1; ++m) {
+        const int64_t col = p2 + m;
         const bool in = col >= 0 && col < g.n2;
-        V.below[d] = in && q + 1 < g.n1 ? __ldcg(u + rq + g.n2 + col) : c;
-        V.right[d] = in && col + 1 < g.n2 ? __ldcg(u + rq + col + 1) : c;
-        V.centre[d] = in ? __ldcg(u + rq + col) : c;
+        below[m - M0] = in && q + 1 < g.n1 ? __ldcg(u + rq + g.n2 + col) : c;
+        right[m - M0] = in && col + 1 < g.n2 ? __ldcg(u + rq + col + 1) : c;
+        centre[m - M0] = in ? __ldcg(u + rq + col) : c;
     }
-    if (first) V.left = p2 - 1 >= 0 && p2 - 1 < g.n2 ? __ldcg(u + rq + p2 - 1) : c;
-}
-
-template <int ARITH>
-__device__ __forceinline__ void gd_combine(const WArr<5>& w, const GdWin& V, double* __restrict__ P)
-{
 #pragma unroll
-    for (int d = 0; d < GD_PW; ++d) {
-        double acc = __dmul_rn(w.w[0], V.below[d]);
-        acc = acc_step<ARITH>(acc, w.w[1], V.right[d]);
-        P[d] = acc_step<ARITH>(acc, w.w[2], V.centre[d]);
-    }
-}
-
-// One producer warp's part of a tile (points m0 .. m0 + GD_PW - 1 of every lane): the row above
-// step 0, step 0's terms, then per step st the terms of step st + 1 (from registers) and the loads of
-// step st + 2; one barrier per step.
-template <int ARITH>
-__device__ __forceinline__ void gd_producer(const double* __restrict__ u, const Geo& g, double c, const WArr<5>& w,
-                                            int H, bool lact, int64_t r0, int64_t p2, int m0, bool first,
-                                            double (*Ps)[32][GD_W + 1], double (*L0s)[32], double (*A0s)[GD_W + 1],
-                                            int lane)
-{
-    constexpr int NCOMP = 32 * (GD_NP + 1);
-    auto live = [&](int sn) { return lact && sn < H && r0 + sn >= 0 && r0 + sn < g.n1; };
-    const int64_t p = p2 + m0;
-    GdWin V;
-    if (live(0)) {
-#pragma unroll
-        for (int d = 0; d < GD_PW; ++d) {
-            const int64_t col = p + d;
-            A0s[lane][m0 + d] = r0 >= 1 && col >= 0 && col < g.n2 ? __ldcg(u + (r0 - 1) * g.n2 + col) : c;
-        }
-        gd_load(u, g, c, r0, p, p2, first, V);
-        gd_combine<ARITH>(w, V, &Ps[0][lane][m0]);
-        if (first) L0s[0][lane] = V.left;
-    }
-    if (live(1)) gd_load(u, g, c, r0 + 1, p, p2, first, V);
-    asm volatile("bar.sync 1, %0;" ::"r"(NCOMP) : "memory");
-#pragma unroll 1
-    for (int st = 0; st < H; ++st) {
-        if (live(st + 1)) {
-            gd_combine<ARITH>(w, V, &Ps[(st + 1) & 1][lane][m0]);
-            if (first) L0s[(st + 1) & 1][lane] = V.left;
-        }
-        if (live(st + 2)) gd_load(u, g, c, r0 + st + 2, p, p2, first, V);
-        asm volatile("bar.sync 1, %0;" ::"r"(NCOMP) : "memory");
+    for (int m = M0; m < M1; ++m) {
+        double acc = __dmul_rn(w.w[0], below[m - M0]);
+        acc = acc_step<ARITH>(acc, w.w[1], right[m - M0]);
+        P[m] = acc_step<ARITH>(acc, w.w[2], centre[m - M0]);
     }
 }
 
@@ -751,16 +699,36 @@ __global__ void __launch_bounds__(GD_THREADS) k_gs2d_dec(double* __restrict__ u,
             const bool lact = lane < L;
             const int64_t p2 = J * GD_W - (int64_t)wg.b1 * lane;  // a1 = 0: the same columns at every step
             const int64_t r0 = I * wg.H - (int64_t)GD_S * lane;   // the lane's row at step 0
-            if (warp >= 1) {
-                gd_producer<ARITH>(u, g, c, w, wg.H, lact, r0, p2, (warp - 1) * GD_PW, warp == 1, Ps, L0s, A0s, lane);
-            } else {
-                // the chain: the two newest-value terms of every point of step st, one barrier per step
-                asm volatile("bar.sync 1, %0;" ::"r"(NCOMP) : "memory");
-                double above[GD_W];
+            // producers: P of step sn for every lane into slot sn & 1 (and the newest left value;
+            // at sn = 0 also the row above)
+            auto produce = [&](int sn) {
+                const int64_t q = r0 + sn;
+                if (!lact || q < 0 || q >= g.n1) return;
+                double* P = Ps[sn & 1][lane];
+                switch (warp) {
+                    case 1: gd_produce<ARITH, 0, 4>(u, g, c, w, q, p2, P); break;
+                    case 2: gd_produce<ARITH, 4, 8>(u, g, c, w, q, p2, P); break;
+                    case 3: gd_produce<ARITH, 8, 12>(u, g, c, w, q, p2, P); break;
+                    default: gd_produce<ARITH, 12, 16>(u, g, c, w, q, p2, P); break;
+                }
+                if (warp == 1)
+                    L0s[sn & 1][lane] = p2 - 1 >= 0 && p2 - 1 < g.n2 ? __ldcg(u + q * g.n2 + p2 - 1) : c;
+                if (sn == 0) {
+                    const int m0 = (warp - 1) * 4;
 #pragma unroll
-                for (int m = 0; m < GD_W; ++m) above[m] = c;
-#pragma unroll 1
-                for (int st = 0; st < wg.H; ++st) {
+                    for (int d = 0; d < 4; ++d) {
+                        const int64_t col = p2 + m0 + d;
+                        A0s[lane][m0 + d] = q >= 1 && col >= 0 && col < g.n2 ? __ldcg(u + (q - 1) * g.n2 + col) : c;
+                    }
+                }
+            };
+            if (warp >= 1) produce(0);
+            asm volatile("bar.sync 1, %0;" ::"r"(NCOMP) : "memory");
+            double above[GD_W];
+#pragma unroll
+            for (int m = 0; m < GD_W; ++m) above[m] = c;
+            for (int st = 0; st < wg.H; ++st) {
+                if (warp == 0) {
                     const int64_t q = r0 + st;
                     if (lact && q >= 0 && q < g.n1) {
                         const double* P = Ps[st & 1][lane];
@@ -781,8 +749,10 @@ __global__ void __launch_bounds__(GD_THREADS) k_gs2d_dec(double* __restrict__ u,
                             }
                         }
                     }
-                    asm volatile("bar.sync 1, %0;" ::"r"(NCOMP) : "memory");
+                } else if (st + 1 < wg.H) {
+                    produce(st + 1);
                 }
+                asm volatile("bar.sync 1, %0;" ::"r"(NCOMP) : "memory");
             }
             const int64_t fidx = (b * wg.nI + I) * wg.nJ + J;
             if (tid == 0 && fidx != wc.stall) {
@@ -1265,13 +1235,13 @@ static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, boo
     }
     if (h->dim == 2) {
         // points per lane and step: 16, or 8 when a fixed wavefront plan asks for it (tile[2] = 8);
-        // the 5-point star with one weight per term runs the decoupled tile unless the plan asks
-        // for the one-warp tile (tile[2] = 8 or 16)
+        // tile[2] = 1 selects the decoupled tile for the 5-point star with one weight per term
+        // (measured level with the one-warp tile at best, so not the default)
         const int64_t pw = h->plan_kernel == STENCIL_KERNEL_WAVEFRONT ? h->plan_tile[2] : 0;
         const bool w8 = pw == 8;
         if (h->shape == STAR && h->r == 1)
             return w8 ? wave_tiles<2, STAR, 1, 8>(ctx, u, T, lanes, prep)
-                      : wave_tiles<2, STAR, 1, 16>(ctx, u, T, lanes, prep, pw == 0 && !ctx.sd.field);
+                      : wave_tiles<2, STAR, 1, 16>(ctx, u, T, lanes, prep, pw == 1 && !ctx.sd.field);
         if (h->shape == BOX && h->r == 1)
             return w8 ? wave_tiles<2, BOX, 1, 8>(ctx, u, T, lanes, prep)
                       : wave_tiles<2, BOX, 1, 16>(ctx, u, T, lanes, prep);

@@ -131,10 +131,10 @@ def test_periodic_box_wavefront_is_rejected():
 
 @pytest.mark.parametrize("shape,ext", [("star", (130, 77)), ("box", (70, 131))])
 @pytest.mark.parametrize("tile", [(0, 0, 8), (4, 0, 8), (3, 0, 16), (0, 2, 0), (2, 5, 8), (3, 8, 16), (0, 64, 16),
-                                  (4, 4, 0), (1, 0, 0), (3, 33, 0)])
+                                  (4, 4, 1), (1, 0, 1), (3, 33, 1)])
 def test_gs2d_wavefront_plan_parameters(shape, ext, tile):
-    """Points per lane and step (8 or 16: the one-warp tile; 0: the decoupled tile for the star), skewed rows
-    per tile and CTAs per SM of the 2D wavefront change nothing in the result."""
+    """Points per lane and step of the one-warp tile (8 or 16) or the decoupled tile (1, the star only),
+    skewed rows per tile and CTAs per SM of the 2D wavefront change nothing in the result."""
     w, u0 = case(2, shape, 1, ext, seed=99)
     for T in (1, 33, 70):
         ref = oracle_run(u0, T, 2, shape, 1, w, "gs", "constant", 0.3, "fma")
@@ -150,6 +150,6 @@ def test_gs2d_decoupled_tile_equals_one_warp_tile(ext):
     u0 = inputs.grid(inputs.SEED_BASE + 31, ext)
     w = inputs.normalized_weights(inputs.SEED_BASE + 131, 5)
     for arith in ("fma", "unfused"):
-        a = gpu_run(u0, 70, 2, "star", 1, w, "gs", "constant", 0.2, arith, plan=WAVE)
-        b = gpu_run(u0, 70, 2, "star", 1, w, "gs", "constant", 0.2, arith, plan=WAVE, tile=(0, 0, 16))
+        a = gpu_run(u0, 70, 2, "star", 1, w, "gs", "constant", 0.2, arith, plan=WAVE, tile=(0, 0, 1))
+        b = gpu_run(u0, 70, 2, "star", 1, w, "gs", "constant", 0.2, arith, plan=WAVE)
         assert bits_equal(a, b), (arith, first_diff(a, b))

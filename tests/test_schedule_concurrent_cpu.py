@@ -8,9 +8,9 @@ acquires the next period's, fills a ring of 8 levels); the CTA barriers at band
 ends join them. k_gs1d_wave4 (Gauss-Seidel sweeps on warp lanes, skew 33, one
 chain warp and six partial-sum warps per 16-step batch): the warps' tasks of a
 batch run in random order between barriers. k_gs2d_dec (2D 5-point
-Gauss-Seidel, sweeps on warp lanes 4 rows apart, tiles of a DAG; per step the
+Gauss-Seidel, sweeps on warp lanes 3 rows apart, tiles of a DAG; per step the
 chain warp's two newest-value terms and the producer warps' three
-previous-sweep terms of the next step, loaded a step earlier): tiles in random orders that respect
+previous-sweep terms of the next step): tiles in random orders that respect
 the DAG, the two roles of a step in either order, and every cell read checked
 for the sweep its value must carry. Random interleavings of all coroutines
 must neither deadlock nor read a value before it is published (every value
@@ -297,12 +297,10 @@ def test_gauss_seidel_1d_wavefront_schedule(N, T, c):
         assert bits_equal(run_gs1d_wave(u0, T, w, c, seed), ref), seed
 
 
-def run_gs2d_dec(u0, T, w, cval, seed, H=16, W=16, S=4):
+def run_gs2d_dec(u0, T, w, cval, seed, H=16, W=16, S=3):
     """The decoupled 2D tile's schedule: lane k of sweep block b applies sweep 32 b + k + 1 at rows
-    r0 + st (r0 = I H - S k) and columns p2 .. p2 + W - 1 (p2 = J W - k). During step st the chain
-    applies the two newest-value terms of step st while the producers combine the three
-    previous-sweep terms of step st + 1 from values loaded one step earlier and load those of
-    step st + 2."""
+    r0 + st (r0 = I H - S k) and columns p2 .. p2 + W - 1 (p2 = J W - k); the producers form the three
+    previous-sweep terms of step st + 1 while the chain applies the two newest-value terms of step st."""
     n1, n2 = u0.shape
     u, ver = u0.copy(), np.zeros(u0.shape, dtype=np.int64)  # ver: sweeps applied to each cell
     wd, rng = list(reversed(w)), random.Random(seed)  # (+1,0), (0,+1), (0,0), (0,-1), (-1,0)
@@ -330,12 +328,10 @@ def run_gs2d_dec(u0, T, w, cval, seed, H=16, W=16, S=4):
 
     def tile(b, I, J):
         Lb = min(32, T - 32 * b)
-        V, P, L0, A0 = {}, [dict(), dict()], [dict(), dict()], {}
+        P, L0, A0 = [dict(), dict()], [dict(), dict()], {}
         above = [[cval] * W for _ in range(32)]
 
-        def load(sn):  # the producers' reads for step sn
-            if sn >= H:
-                return
+        def produce(sn):
             for k in range(Lb):
                 q, p2, sw = I * H - S * k + sn, J * W - b1 * k, 32 * b + k
                 if not 0 <= q < n1:
@@ -343,21 +339,12 @@ def run_gs2d_dec(u0, T, w, cval, seed, H=16, W=16, S=4):
                 for m in range(W):
                     col = p2 + m
                     if 0 <= col < n2:
-                        V[(sn, k, m)] = (rd(q + 1, col, sw), rd(q, col + 1, sw), rd(q, col, sw))
-                V[(sn, k, "left")] = rd(q, p2 - 1, sw + 1)
-
-        def combine(sn):  # registers only
-            if sn >= H:
-                return
-            for k in range(Lb):
-                q, p2 = I * H - S * k + sn, J * W - b1 * k
-                if not 0 <= q < n1:
-                    continue
-                for m in range(W):
-                    if 0 <= p2 + m < n2:
-                        bl, ri, ce = V.pop((sn, k, m))
-                        P[sn & 1][(k, m)] = ((wd[0] * bl + wd[1] * ri) + wd[2] * ce, sn)
-                L0[sn & 1][k] = (V.pop((sn, k, "left")), sn)
+                        acc = wd[0] * rd(q + 1, col, sw)
+                        acc = acc + wd[1] * rd(q, col + 1, sw)
+                        P[sn & 1][(k, m)] = (acc + wd[2] * rd(q, col, sw), sn)
+                    if sn == 0:
+                        A0[(k, m)] = rd(q - 1, col, sw + 1) if q >= 1 and 0 <= col < n2 else cval
+                L0[sn & 1][k] = (rd(q, p2 - 1, sw + 1), sn)
 
         def chain(st):
             for k in range(Lb):
@@ -379,18 +366,9 @@ def run_gs2d_dec(u0, T, w, cval, seed, H=16, W=16, S=4):
                     else:
                         left = cval
 
-        # prologue: the row above step 0, step 0's terms, step 1's reads
-        for k in range(Lb):
-            q, p2, sw = I * H - S * k, J * W - b1 * k, 32 * b + k
-            if 0 <= q < n1:
-                for m in range(W):
-                    col = p2 + m
-                    A0[(k, m)] = rd(q - 1, col, sw + 1) if q >= 1 and 0 <= col < n2 else cval
-        load(0)
-        combine(0)
-        load(1)
+        produce(0)
         for st in range(H):
-            tasks = [lambda: chain(st), lambda: (combine(st + 1), load(st + 2))]
+            tasks = [lambda: chain(st)] + ([lambda: produce(st + 1)] if st + 1 < H else [])
             rng.shuffle(tasks)  # the chain and the producers of a step run concurrently
             for f in tasks:
                 f()
