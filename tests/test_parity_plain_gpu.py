@@ -91,3 +91,36 @@ def test_argument_errors():
     with pytest.raises(S.StencilError):
         st.run(torch.zeros(8, dtype=torch.float64, device="cuda"), -1)
     st.close()
+
+
+@pytest.mark.parametrize("dim,ext,kernel,tb,T", [(2, (300, 257), 1, 0, 9), (3, (40, 33, 70), 1, 0, 6),
+                                                 (1, (20000,), 2, 8, 37), (2, (130, 515), 2, 4, 11)])
+def test_programmatic_launches_replay_in_a_cuda_graph(dim, ext, kernel, tb, T):
+    """Plain steps and blocked passes are launched with programmatic stream serialization; a run captured
+    into a CUDA graph (the launches become programmatic edges) replays to the oracle's grid, after
+    other work on the same stream."""
+    import torch
+    from paper_2010_04868_gb300 import stencil as S
+    w, u0 = case(dim, "star", 1, ext, seed=dim + 17)
+    ref = oracle_run(u0, T, dim, "star", 1, w, "jacobi", "constant", 0.25, "fma")
+    st = S.Stencil(dim, 0, 1, list(w), S.STENCIL_JACOBI, S.STENCIL_BC_CONSTANT, 0.25)
+    st.set_plan(kernel, tb)
+    u = torch.from_numpy(u0.copy()).cuda()
+    scratch = torch.empty_like(u)
+    src = torch.from_numpy(u0.copy()).cuda()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            u.copy_(src)        # a kernel of another library right before the first programmatic launch
+            st.run(u, T, scratch=scratch, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        u.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert st.status() == 0
+        got = u.cpu().numpy()
+        assert bits_equal(got, ref), first_diff(got, ref)
+    st.close()
