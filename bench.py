@@ -48,6 +48,14 @@ NCU_TRAFFIC = {("2d9p", "plain", 1, (0, 0, 0)): 134_256_128 + 94_363_392,
                ("2d9p", "diamond", 16, (0, 88, 88)): (464_250_112 + 175_210_752) // 4}
 
 
+def workload_config(world):
+    """The workload both arms (the library and the oracle) report on."""
+    return {"workload": "Jacobi 2D 5-point star + 9-point box, 4096x4096 FP64, zero Dirichlet halo, "
+                        "T=1000 each, autotuned kernel", "grids": "2 x 4096^2", "T": T_STEPS,
+            "l2": "inputs (2 x 128 MiB grid + scratch) exceed L2; 512 MiB flush between steps",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -284,10 +292,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 uniform [0,1), seeded normalised weights)",
-            "config": {"workload": "Jacobi 2D 5-point star + 9-point box, 4096x4096 FP64, zero Dirichlet halo, "
-                                   "T=1000 each, autotuned kernel", "grids": "2 x 4096^2", "T": T_STEPS,
-                       "l2": "inputs (2 x 128 MiB grid + scratch) exceed L2; 512 MiB flush between steps",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": workload_config(world),
             "per_stencil_gstencil_s": per_stencil, "plain_kernel_gstencil_s": plain, "plans": plans,
             "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches),
             "e2e": e2e, "cpu_baseline": cpu,
@@ -371,8 +376,7 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "Jacobi 2D 5-point star + 9-point box, 4096x4096 FP64, zero Dirichlet halo, "
-                                   "T=1000 each (sampled)"},
+            "config": workload_config(world),
             "cpu_baseline": {"value": round(value, 4), "unit": "GStencil/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "GStencil/s", "h2d_bytes_per_step": 0,
