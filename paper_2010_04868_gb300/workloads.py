@@ -87,9 +87,11 @@ def config_weights(name):
     return list(inputs.normalized_weights(inputs.SEED_BASE + w, k_points(dim, shape, RADIUS.get(name, 1))))
 
 
-def config_field(name):
-    dim, shape, _, ext, _, _, seed = CONFIGS[name]
-    return inputs.normalized_field(inputs.SEED_BASE + seed, k_points(dim, shape, RADIUS.get(name, 1)), ext)
+def config_field(name, ext=None):
+    """The configuration's weight field, on its own extents or on ext (a smaller case)."""
+    dim, shape, _, ext0, _, _, seed = CONFIGS[name]
+    return inputs.normalized_field(inputs.SEED_BASE + seed, k_points(dim, shape, RADIUS.get(name, 1)),
+                                   ext0 if ext is None else ext)
 
 
 def config_grid(name):
@@ -108,7 +110,7 @@ def run(name, kernel="auto", T=None, reps=2, tb=0, tile=(0, 0, 0), sm_mhz=2070.0
     u0 = torch.from_numpy(config_grid(name) if ext == ext0 else inputs.grid(inputs.SEED_BASE + 10, ext)).cuda()
     st = S.Stencil(dim, shape, r, config_weights(name), method, bc)
     if name in FIELD:
-        st.set_field(torch.from_numpy(config_field(name)).cuda())
+        st.set_field(torch.from_numpy(config_field(name, ext)).cuda())
     if kernel != "auto":
         st.set_plan(KERNELS[kernel], tb, tile)
     u = u0.clone()
