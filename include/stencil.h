@@ -54,7 +54,8 @@ extern "C" {
 #define STENCIL_ENOMEM (-3)       /* device allocation failed */
 #define STENCIL_ECUDA (-4)        /* a CUDA call or kernel launch failed */
 #define STENCIL_ETIMEOUT (-5)     /* a device-side bounded wait gave up */
-#define STENCIL_EBOUNDS (-6)      /* a device-side index check failed */
+#define STENCIL_EBOUNDS (-6)      /* a device-side index check failed (reserved: no kernel of this
+                                     build checks indices at run time; none reports it) */
 
 /* Stencil shape (Section 1 taxonomy). */
 #define STENCIL_STAR 0
