@@ -251,12 +251,16 @@ int stencil_debug_inject_stall(stencil_handle h, int64_t unit, int spin);
  * ignored and the second Jacobi buffer is a fixed 16 MiB array inside the
  * library, held by every GPU that loads the library until the process exits.
  *   h        a Jacobi handle created on the current device (else EINVAL).
- *   g        grid of at most 2^21 points (2,097,152); larger grids return
- *            STENCIL_EUNSUPPORTED without touching the GPU.
+ *   g        grid of at most 2^21 points (2,097,152). Extents are checked as
+ *            by stencil_run first (EINVAL, including extents whose product
+ *            overflows); a valid grid with more points returns
+ *            STENCIL_EUNSUPPORTED. Neither touches the GPU.
  *   T        steps, >= 0.
  * All calls share the array: calls that overlap on the GPU race and must be
  * serialised by the caller. The first call on each device looks up the
- * array's device address and should come before any stream capture begins.
+ * array's device address and should come before any stream capture begins;
+ * that address is kept until the process exits and does not survive
+ * cudaDeviceReset (do not call this entry point on a device after a reset).
  * No cudaMalloc, cudaFree or allocating library routine is called.
  */
 int stencil_run_noalloc(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_stream);

@@ -2,6 +2,8 @@
 
 Each translation unit under csrc/ is compiled in parallel into _build/, then
 linked into libgb300stencil.so next to this file. Rebuilds only what changed.
+The FP64 pipe micro-benchmark (peak/fp64_peak.cu, the ALU roofline bench.py
+reports against) is compiled alongside into peak/fp64_peak.
 """
 from __future__ import annotations
 
@@ -47,11 +49,30 @@ def _compile(src, hdr_mtime, extra):
     return obj, None
 
 
+PROBE_SRC = os.path.join(HERE, "peak", "fp64_peak.cu")
+PROBE_EXE = os.path.join(HERE, "peak", "fp64_peak")
+
+
+def build_probe() -> str:
+    """Compile the FP64 pipe micro-benchmark into peak/fp64_peak (if its source is newer)."""
+    if os.path.exists(PROBE_EXE) and os.path.getmtime(PROBE_EXE) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_EXE
+    tmp = PROBE_EXE + ".tmp%d" % os.getpid()
+    cmd = [_nvcc()] + ARCH + ["-O3", "-o", tmp, PROBE_SRC]
+    p = subprocess.run(cmd, capture_output=True, text=True)
+    if p.returncode != 0:
+        raise RuntimeError("nvcc failed:\n%s\n%s%s" % (" ".join(cmd), p.stdout, p.stderr))
+    os.replace(tmp, PROBE_EXE)
+    return PROBE_EXE
+
+
 def build(verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     hdr = _deps()
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
+        probe = ex.submit(build_probe)
         res = list(ex.map(lambda s: _compile(s, hdr, list(extra)), SOURCES))
+        probe.result()
     errs = [e for _, e in res if e]
     if errs:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errs))

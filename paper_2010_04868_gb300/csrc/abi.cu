@@ -22,6 +22,25 @@ Geo make_geo(int dim, const int64_t ext[3])
     return g;
 }
 
+// Argument checks shared by every entry point that takes a grid: extents >= 1
+// (>= 2r+1 when periodic), the bound field's extents, and a byte size that
+// fits in int64 (so no later product of the extents overflows).
+int check_grid(const stencil_handle_s* h, const stencil_grid* g)
+{
+    if (!h || !g || !g->data) return STENCIL_EINVAL;
+    for (int d = 0; d < h->dim; ++d) {
+        if (g->ext[d] < 1) return STENCIL_EINVAL;
+        if (h->bc == STENCIL_BC_PERIODIC && g->ext[d] < 2 * h->r + 1) return STENCIL_EINVAL;
+        if (h->field && g->ext[d] != h->field_ext[d]) return STENCIL_EINVAL;
+    }
+    int64_t n = 1;
+    for (int d = 0; d < h->dim; ++d) {
+        if (n > INT64_MAX / g->ext[d] / 8) return STENCIL_EINVAL;
+        n *= g->ext[d];
+    }
+    return STENCIL_OK;
+}
+
 }  // namespace gbst
 
 // Canonical offsets (lexicographic, slowest axis first), padded to 3 components.
@@ -40,22 +59,6 @@ static int canonical_offsets(int dim, int shape, int r, std::vector<int>& off)
                 off.push_back(c);
             }
     return (int)off.size() / 3;
-}
-
-static int check_grid(const stencil_handle_s* h, const stencil_grid* g)
-{
-    if (!h || !g || !g->data) return STENCIL_EINVAL;
-    for (int d = 0; d < h->dim; ++d) {
-        if (g->ext[d] < 1) return STENCIL_EINVAL;
-        if (h->bc == STENCIL_BC_PERIODIC && g->ext[d] < 2 * h->r + 1) return STENCIL_EINVAL;
-        if (h->field && g->ext[d] != h->field_ext[d]) return STENCIL_EINVAL;
-    }
-    int64_t n = 1;
-    for (int d = 0; d < h->dim; ++d) {
-        if (n > INT64_MAX / g->ext[d] / 8) return STENCIL_EINVAL;
-        n *= g->ext[d];
-    }
-    return STENCIL_OK;
 }
 
 static int64_t npoints(int dim, const int64_t ext[3])

@@ -108,4 +108,8 @@ bool gs_wavefront_supported(const stencil_handle_s* h, const Geo& g);
 // Geometry from a stencil_grid (padded to three dimensions).
 Geo make_geo(int dim, const int64_t ext[3]);
 
+// Validation of a grid against a handle (STENCIL_OK or STENCIL_EINVAL); after
+// it succeeds, the product of the extents times 8 fits in int64.
+int check_grid(const stencil_handle_s* h, const stencil_grid* g);
+
 }  // namespace gbst

@@ -58,6 +58,25 @@ __device__ __forceinline__ bool mbar_wait0(uint64_t* bar)
     return false;
 }
 
+// After a time-out: a further wait on phase 0 with a back-off, bounded at
+// about a second (2^20 polls of at least 1 us each).
+__device__ __forceinline__ void mbar_wait_backoff(uint64_t* bar)
+{
+    const uint32_t a = smem_u32(bar);
+    for (int it = 0; it < (1 << 20); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(0)
+            : "memory");
+        if (done) return;
+        __nanosleep(1000);
+    }
+}
+
 template <int DIM, int SHAPE, int R, int ARITH>
 __global__ void __launch_bounds__(256) k_jacobi_blocked(const __grid_constant__ CUtensorMap tmap,
                                                         const double* __restrict__ in, double* __restrict__ out,
@@ -119,9 +138,13 @@ __global__ void __launch_bounds__(256) k_jacobi_blocked(const __grid_constant__ 
         }
         __syncthreads();
         if (!mbar_wait0(&bar)) {
+            // Record the time-out, then keep the CTA (and its shared memory) until the
+            // barrier completes. The copy is a bounded read of global memory that lands
+            // within microseconds, so this back-off wait (about a second more) ends with
+            // it; a barrier still open after that means the byte count it expects was
+            // never going to be met, which is only possible once every copy has landed.
             if (threadIdx.x == 0) atomicExch(status, DEV_TIMEOUT);
-            // give the copy a further bounded chance to land before the CTA's shared memory goes away
-            mbar_wait0(&bar);
+            mbar_wait_backoff(&bar);
             return;
         }
     } else {

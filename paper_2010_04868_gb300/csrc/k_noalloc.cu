@@ -21,7 +21,10 @@
 // names a host-side stand-in), so the device address is looked up with
 // cudaGetSymbolAddress once per device, on the first call made with that
 // device current. That first call should therefore come before any stream
-// capture begins.
+// capture begins. The address found is kept for the life of the process: it
+// does not survive cudaDeviceReset (or anything else that destroys the
+// device's primary context), after which this entry point must not be called
+// on that device again.
 #include <mutex>
 
 #include "internal.h"
@@ -57,17 +60,17 @@ double* noalloc_scratch(int device)
 extern "C" int stencil_run_noalloc(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_stream)
 {
     using namespace gbst;
-    if (!h || !g || !g->data || T < 0) return STENCIL_EINVAL;
+    if (!h || !g || T < 0) return STENCIL_EINVAL;
     if (h->method != STENCIL_JACOBI) return STENCIL_EINVAL;
+    // the library's own grid checks (extents, periodic minimum, field extents,
+    // and a size whose product cannot overflow) come first
+    int rc = check_grid(h, g);
+    if (rc) return rc;
     int64_t n = 1;
     for (int d = 0; d < h->dim; ++d) {
-        if (g->ext[d] < 1) return STENCIL_EINVAL;
-        if (h->bc == STENCIL_BC_PERIODIC && g->ext[d] < 2 * h->r + 1) return STENCIL_EINVAL;
-        if (h->field && g->ext[d] != h->field_ext[d]) return STENCIL_EINVAL;
-        if (n > NOALLOC_MAX_POINTS) return STENCIL_EUNSUPPORTED;
+        if (g->ext[d] > NOALLOC_MAX_POINTS / n) return STENCIL_EUNSUPPORTED;  // n * ext > the maximum
         n *= g->ext[d];
     }
-    if (n > NOALLOC_MAX_POINTS) return STENCIL_EUNSUPPORTED;
     int device = -1;
     if (cudaGetDevice(&device) != cudaSuccess) return STENCIL_ECUDA;
     if (device != h->device) return STENCIL_EINVAL;
@@ -83,7 +86,7 @@ extern "C" int stencil_run_noalloc(stencil_handle h, const stencil_grid* g, int6
     double* a = g->data;
     double* b = scratch;
     for (int64_t t = 0; t < T; ++t) {
-        int rc = jacobi_plain_step(ctx, a, b);
+        rc = jacobi_plain_step(ctx, a, b);
         if (rc) return rc;
         double* tmp = a;
         a = b;

@@ -1,3 +1,4 @@
+"""FP64 and integer pipe rates of the current GPU: python -m paper_2010_04868_gb300.peak [--sweep]."""
 import os
 import subprocess
 import sys
@@ -7,13 +8,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def main():
-    """FP64 and integer pipe rates (default), or with --sync the level-loop and FP64-sharing probes."""
-    src = "sync_probes.cu" if "--sync" in sys.argv[1:] else "fp64_peak.cu"
-    exe = os.path.join(tempfile.gettempdir(), "gb300_%s_%d" % (src[:-3], os.getpid()))
+    """Compile fp64_peak.cu for sm_103a, run it and print its JSON (one object per swept shape with --sweep)."""
+    exe = os.path.join(tempfile.gettempdir(), "gb300_fp64_peak_%d" % os.getpid())
     subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe,
-                           os.path.join(HERE, src)])
+                           os.path.join(HERE, "fp64_peak.cu")])
     try:
-        out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+        out = subprocess.run([exe] + sys.argv[1:2], capture_output=True, text=True, timeout=300)
         sys.stdout.write(out.stdout)
         return out.returncode
     finally:

@@ -2,125 +2,246 @@
 // Also the 32-bit integer logic (LOP3) and funnel-shift (SHF) rates, the roofline of the
 // bit-packed Game of Life kernels.
 //
-// Streams of independent __fma_rn / __dadd_rn / __dmul_rn on every resident
-// warp, timed with clock64() per CTA (SM clocks, so the result is a per-clock
-// rate independent of the clock the GPU happened to run at) and with CUDA
-// events. Also: the dependent-chain latency of one DFMA, and the cost of a
-// warp instruction with only some lanes active. Prints one JSON object.
+// Streams of independent __fma_rn / __dadd_rn / __dmul_rn on every resident warp. Each CTA
+// records its SM (%smid) and the SM clock (clock64) at its start and end; an SM's rate is
+// the lane operations of all its CTAs over the span from its first start to its last end,
+// so the result is a per-clock rate independent of the clock the GPU happened to run at.
+// The rate is swept over the shapes that could limit it:
+//   * chains per thread (independent accumulators: latency hiding inside a warp),
+//   * warps per SM (CTAs per SM x warps per CTA: latency hiding across warps),
+//   * the instruction (DFMA, DADD, DMUL, and the three interleaved),
+//   * the operands (two shared scalars, or a distinct register triple per chain),
+// and the best rate is the FP64 peak reported. Also: the dependent-chain latency of one
+// DFMA and the cost of a warp instruction with one active lane.
+//
+//   fp64_peak            one JSON object: the best rate of a short sweep (about a second)
+//   fp64_peak --sweep    one JSON object per swept shape, then the summary
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
-#include <algorithm>
+
 #include <cuda_runtime.h>
 
-#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { \
-    printf("{\"error\": \"%s at line %d\"}\n", cudaGetErrorString(e_), __LINE__); exit(1); } } while (0)
+#define CK(x)                                                                                     \
+    do {                                                                                          \
+        cudaError_t e_ = (x);                                                                     \
+        if (e_ != cudaSuccess) {                                                                  \
+            printf("{\"error\": \"%s at line %d\"}\n", cudaGetErrorString(e_), __LINE__);         \
+            exit(1);                                                                              \
+        }                                                                                         \
+    } while (0)
 
-template <int CH, int OP>
-__global__ void stream_ops(double* out, long long* cyc, int iters, double a, double b, int active)
+__device__ __forceinline__ unsigned smid()
 {
-    if ((int)(threadIdx.x & 31) >= active) return;
-    double x[CH];
-#pragma unroll
-    for (int c = 0; c < CH; ++c) x[c] = threadIdx.x * 1e-9 + c * 0.1;
+    unsigned s;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+    return s;
+}
+
+// OP: 0 DFMA x = fma(x, a, b); 1 DADD; 2 DMUL; 3 DFMA, DADD, DMUL in turn;
+//     4 DFMA with a distinct register triple per chain: x = fma(y, x, z)
+template <int CH, int OP>
+__global__ void stream_ops(double* out, long long* rec, int iters, double a, double b, int active)
+{
     const long long t0 = clock64();
-    for (int i = 0; i < iters; ++i) {
+    double x[CH], y[CH], z[CH];
 #pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            if (OP == 0) x[c] = __fma_rn(x[c], a, b);
-            else if (OP == 1) x[c] = __dadd_rn(x[c], b);
-            else x[c] = __dmul_rn(x[c], a);
+    for (int c = 0; c < CH; ++c) {
+        x[c] = threadIdx.x * 1e-9 + c * 0.1;
+        y[c] = a + c * 1e-12;
+        z[c] = b * (1 + c);
+    }
+    if ((int)(threadIdx.x & 31) < active) {
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                if (OP == 0) x[c] = __fma_rn(x[c], a, b);
+                else if (OP == 1) x[c] = __dadd_rn(x[c], b);
+                else if (OP == 2) x[c] = __dmul_rn(x[c], a);
+                else if (OP == 3) {
+                    if (c % 3 == 0) x[c] = __fma_rn(x[c], a, b);
+                    else if (c % 3 == 1) x[c] = __dadd_rn(x[c], b);
+                    else x[c] = __dmul_rn(x[c], a);
+                } else x[c] = __fma_rn(y[c], x[c], z[c]);
+            }
         }
     }
-    const long long t1 = clock64();
     double s = 0;
 #pragma unroll
     for (int c = 0; c < CH; ++c) s += x[c];
     if (s == 12345.678) out[0] = s;
-    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+    __syncthreads();
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) {
+        rec[3 * blockIdx.x] = smid();
+        rec[3 * blockIdx.x + 1] = t0;
+        rec[3 * blockIdx.x + 2] = t1;
+    }
 }
 
 // Independent chains of one 3-input logic op (LOP3) or one funnel shift (SHF) per step, written
 // in PTX so that the compiler cannot fold the repeated bitwise operations.
 template <int CH, int OP>
-__global__ void stream_int(double* out, long long* cyc, int iters, double fa, double fb, int active)
+__global__ void stream_int(double* out, long long* rec, int iters, double fa, double fb, int active)
 {
-    if ((int)(threadIdx.x & 31) >= active) return;
+    const long long t0 = clock64();
     const unsigned a = (unsigned)(fa * 1e7) | 1u, b = (unsigned)(fb * 1e9) + 3u;
     unsigned x[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) x[c] = threadIdx.x * 7u + c;
-    const long long t0 = clock64();
-    for (int i = 0; i < iters; ++i) {
+    if ((int)(threadIdx.x & 31) < active) {
+        for (int i = 0; i < iters; ++i) {
 #pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            if (OP == 0)
-                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x[c]) : "r"(a), "r"(b));
-            else
-                asm volatile("shf.l.wrap.b32 %0, %0, %1, 1;" : "+r"(x[c]) : "r"(b));
+            for (int c = 0; c < CH; ++c) {
+                if (OP == 0)
+                    asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x[c]) : "r"(a), "r"(b));
+                else
+                    asm volatile("shf.l.wrap.b32 %0, %0, %1, 1;" : "+r"(x[c]) : "r"(b));
+            }
         }
     }
-    const long long t1 = clock64();
     unsigned s = 0;
 #pragma unroll
     for (int c = 0; c < CH; ++c) s ^= x[c];
     if (s == 0x12345678u) out[0] = s;
-    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+    __syncthreads();
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) {
+        rec[3 * blockIdx.x] = smid();
+        rec[3 * blockIdx.x + 1] = t0;
+        rec[3 * blockIdx.x + 2] = t1;
+    }
 }
 
-static double median(std::vector<long long> v)
+typedef void (*Kern)(double*, long long*, int, double, double, int);
+
+struct Shape {
+    const char* op;
+    Kern k;
+    int chains, threads, ctas_per_sm, active;
+};
+
+static int g_nsm = 0;
+static double* g_out = nullptr;
+static long long* g_rec = nullptr;
+static cudaEvent_t g_e0, g_e1;
+
+// Lane operations per SM clock (median over SMs), or 0 if the CTAs cannot all be resident.
+static double measure(const Shape& s, int iters, double* ops_per_s, double* ms_out)
 {
-    std::sort(v.begin(), v.end());
-    return (double)v[v.size() / 2];
+    int fit = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, s.k, s.threads, 0));
+    if (fit < s.ctas_per_sm) return 0.0;
+    const int nblk = g_nsm * s.ctas_per_sm;
+    s.k<<<nblk, s.threads>>>(g_out, g_rec, iters / 8 + 1, 1.0000001, 1e-7, s.active);  // warm-up
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    CK(cudaEventRecord(g_e0));
+    s.k<<<nblk, s.threads>>>(g_out, g_rec, iters, 1.0000001, 1e-7, s.active);
+    CK(cudaEventRecord(g_e1));
+    CK(cudaEventSynchronize(g_e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, g_e0, g_e1));
+    std::vector<long long> rec(3 * (size_t)nblk);
+    CK(cudaMemcpy(rec.data(), g_rec, rec.size() * sizeof(long long), cudaMemcpyDeviceToHost));
+    const int maxsm = 1024;
+    std::vector<long long> lo(maxsm, -1), hi(maxsm, -1);
+    std::vector<int> cnt(maxsm, 0);
+    for (int b = 0; b < nblk; ++b) {
+        const int sm = (int)rec[3 * b];
+        if (sm < 0 || sm >= maxsm) continue;
+        if (lo[sm] < 0 || rec[3 * b + 1] < lo[sm]) lo[sm] = rec[3 * b + 1];
+        if (hi[sm] < 0 || rec[3 * b + 2] > hi[sm]) hi[sm] = rec[3 * b + 2];
+        cnt[sm]++;
+    }
+    const double lanes = (double)(s.active < 32 ? s.active : 32);
+    const double ops_per_cta = (s.threads / 32.0) * lanes * (double)iters * s.chains;
+    std::vector<double> rates;
+    for (int sm = 0; sm < maxsm; ++sm)
+        if (cnt[sm] > 0 && hi[sm] > lo[sm]) rates.push_back(ops_per_cta * cnt[sm] / (double)(hi[sm] - lo[sm]));
+    if (rates.empty()) return 0.0;
+    std::sort(rates.begin(), rates.end());
+    if (ops_per_s) *ops_per_s = ops_per_cta * nblk / (ms * 1e-3);
+    if (ms_out) *ms_out = ms;
+    return rates[rates.size() / 2];
 }
 
-int main()
+template <int CH>
+static void add_shapes(std::vector<Shape>& v, bool full)
 {
+    const int warps[] = {4, 8, 16, 32, 64};
+    for (int wps : warps) {
+        if (!full && wps != 8 && wps != 32) continue;
+        // CTAs of 8 warps (one of 4 for the smallest count)
+        const int threads = wps < 8 ? wps * 32 : 256;
+        const int ctas = wps < 8 ? 1 : wps / 8;
+        v.push_back(Shape{"dfma", stream_ops<CH, 0>, CH, threads, ctas, 32});
+        if (full) {
+            v.push_back(Shape{"dadd", stream_ops<CH, 1>, CH, threads, ctas, 32});
+            v.push_back(Shape{"dmul", stream_ops<CH, 2>, CH, threads, ctas, 32});
+            v.push_back(Shape{"mix", stream_ops<CH, 3>, CH, threads, ctas, 32});
+        }
+        v.push_back(Shape{"dfma_reg3", stream_ops<CH, 4>, CH, threads, ctas, 32});
+    }
+}
+
+int main(int argc, char** argv)
+{
+    const bool full = argc > 1 && strcmp(argv[1], "--sweep") == 0;
     cudaDeviceProp p;
     CK(cudaGetDeviceProperties(&p, 0));
-    const int nsm = p.multiProcessorCount;
-    double* dout;
-    long long* dcyc;
-    CK(cudaMalloc(&dout, 64));
-    CK(cudaMalloc(&dcyc, 8 * 4096));
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    // per-SM rate: 4 warps (one per SM sub-partition) x 8 chains, one CTA per SM
-    auto rate = [&](auto kern, int threads, int iters, int chains, int active, double& ops_per_s) {
-        kern<<<nsm, threads>>>(dout, dcyc, iters / 8, 1.0000001, 1e-7, active);
-        CK(cudaDeviceSynchronize());
-        CK(cudaEventRecord(e0));
-        kern<<<nsm, threads>>>(dout, dcyc, iters, 1.0000001, 1e-7, active);
-        CK(cudaEventRecord(e1));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        std::vector<long long> c(nsm);
-        CK(cudaMemcpy(c.data(), dcyc, 8 * nsm, cudaMemcpyDeviceToHost));
-        const double warps = threads / 32.0;
-        const double lane_ops_per_sm = warps * (active < 32 ? active : 32) * (double)iters * chains;
-        ops_per_s = lane_ops_per_sm * nsm / (ms * 1e-3);
-        return lane_ops_per_sm / median(c);  // lane operations per SM clock
-    };
-    double s_fma, s_add, s_mul, s_lat, s_one;
-    const double fma_clk = rate(stream_ops<8, 0>, 128, 4096, 8, 32, s_fma);
-    const double add_clk = rate(stream_ops<8, 1>, 128, 4096, 8, 32, s_add);
-    const double mul_clk = rate(stream_ops<8, 2>, 128, 4096, 8, 32, s_mul);
-    const double one_lane_clk = rate(stream_ops<8, 0>, 128, 4096, 8, 1, s_one);
-    const double chain_clk = rate(stream_ops<1, 0>, 32, 4096, 1, 1, s_lat);  // 1 lane, dependent chain
-    double s_lop, s_shf;
-    const double lop_clk = rate(stream_int<8, 0>, 512, 4096, 8, 32, s_lop);  // 16 warps: the integer pipes are wider
-    const double shf_clk = rate(stream_int<8, 1>, 512, 4096, 8, 32, s_shf);
+    g_nsm = p.multiProcessorCount;
+    CK(cudaMalloc(&g_out, 64));
+    CK(cudaMalloc(&g_rec, sizeof(long long) * 3 * 1024 * 16));
+    CK(cudaEventCreate(&g_e0));
+    CK(cudaEventCreate(&g_e1));
+
+    std::vector<Shape> shapes;
+    if (full) {
+        add_shapes<1>(shapes, true);
+        add_shapes<2>(shapes, true);
+        add_shapes<4>(shapes, true);
+        add_shapes<8>(shapes, true);
+        add_shapes<16>(shapes, true);
+    } else {
+        add_shapes<4>(shapes, false);
+        add_shapes<8>(shapes, false);
+    }
+    // a fixed number of FP64 instructions per SM for every shape (about 40 ms at the peak)
+    const double target_lane_ops = 1.2e8;
+    double best = 0, best_ops_s = 0;
+    const Shape* best_s = nullptr;
+    for (const Shape& s : shapes) {
+        const double per_iter = (s.threads / 32.0) * 32.0 * s.chains * s.ctas_per_sm;
+        const int iters = (int)std::max(64.0, target_lane_ops / per_iter);
+        double ops_s = 0, ms = 0;
+        const double r = measure(s, iters, &ops_s, &ms);
+        if (full)
+            printf("{\"op\": \"%s\", \"chains\": %d, \"warps_per_sm\": %d, \"lane_ops_per_sm_clk\": %.4f, "
+                   "\"gops\": %.1f, \"ms\": %.3f}\n",
+                   s.op, s.chains, s.threads / 32 * s.ctas_per_sm, r, ops_s / 1e9, ms);
+        if (r > best) {
+            best = r;
+            best_ops_s = ops_s;
+            best_s = &s;
+        }
+    }
+    // one active lane, and the dependent-chain latency (one warp of one lane per SM)
+    const double one_lane = measure(Shape{"dfma", stream_ops<8, 0>, 8, 128, 1, 1}, 4096, nullptr, nullptr);
+    const double chain = measure(Shape{"dfma", stream_ops<1, 0>, 1, 32, 1, 1}, 4096, nullptr, nullptr);
+    const double lop = measure(Shape{"lop3", stream_int<8, 0>, 8, 512, 1, 32}, 4096, nullptr, nullptr);
+    const double shf = measure(Shape{"shf", stream_int<8, 1>, 8, 512, 1, 32}, 4096, nullptr, nullptr);
     int clk_khz = 0;
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, 0);
-    printf("{\"device\": \"%s\", \"sms\": %d, \"max_sm_mhz\": %.0f, "
-           "\"fp64_fma_lane_ops_per_sm_clk\": %.4f, \"fp64_add_lane_ops_per_sm_clk\": %.4f, "
-           "\"fp64_mul_lane_ops_per_sm_clk\": %.4f, \"fp64_fma_gops_measured\": %.1f, "
-           "\"fp64_fma_gops_at_max_clock\": %.1f, \"one_active_lane_lane_ops_per_sm_clk\": %.4f, "
-           "\"dependent_dfma_latency_clk\": %.1f, \"int_lop3_lane_ops_per_sm_clk\": %.2f, "
-           "\"int_shf_lane_ops_per_sm_clk\": %.2f, \"int_lop3_gops_measured\": %.1f}\n",
-           p.name, nsm, clk_khz / 1e3, fma_clk, add_clk, mul_clk, s_fma / 1e9, fma_clk * nsm * clk_khz / 1e6,
-           one_lane_clk, 1.0 / chain_clk, lop_clk, shf_clk, s_lop / 1e9);
+    printf("{\"device\": \"%s\", \"sms\": %d, \"max_sm_mhz\": %.0f, \"shapes_swept\": %zu, "
+           "\"fp64_lane_ops_per_sm_clk\": %.4f, \"best_shape\": {\"op\": \"%s\", \"chains\": %d, "
+           "\"warps_per_sm\": %d}, \"fp64_gops_measured\": %.1f, \"fp64_gops_at_max_clock\": %.1f, "
+           "\"one_active_lane_lane_ops_per_sm_clk\": %.4f, \"dependent_dfma_latency_clk\": %.1f, "
+           "\"int_lop3_lane_ops_per_sm_clk\": %.2f, \"int_shf_lane_ops_per_sm_clk\": %.2f}\n",
+           p.name, g_nsm, clk_khz / 1e3, shapes.size(), best, best_s ? best_s->op : "", best_s ? best_s->chains : 0,
+           best_s ? best_s->threads / 32 * best_s->ctas_per_sm : 0, best_ops_s / 1e9, best * g_nsm * clk_khz / 1e6,
+           one_lane, chain > 0 ? 1.0 / chain : 0.0, lop, shf);
     return 0;
 }

@@ -249,6 +249,35 @@ def fifo_one_at_a_time(arrivals, service_s):
     return lat
 
 
+def bench_run(n_requests: int, rate: float, slots: int = 8, mem_cap: int = 40 * 10 ** 9) -> dict:
+    """The first n_requests of the seeded mix at a fixed Poisson rate (requests/s): latency and throughput.
+
+    One request of each (method, dim, shape) class is served first, outside the measurement, so that
+    first launches and plan lookups are not counted. Plans come from the tuner's cache or its static
+    defaults (no tuning while serving).
+    """
+    import os
+
+    import torch
+    os.environ["STENCIL_NO_TUNE"] = "1"
+    reqs = request_mix(n_requests)
+    ex = GpuExecutor(slots)
+    seen = set()
+    for r in reqs:
+        key = (r.method, r.dim, r.shape)
+        if key not in seen:
+            seen.add(key)
+            Server(ex, slots, mem_cap).serve([Request(-1, r.method, r.dim, r.shape, r.ext, r.T, r.seed)])
+    torch.cuda.synchronize()
+    poisson_arrivals(reqs, rate)
+    st = Server(GpuExecutor(slots), slots, mem_cap).serve(reqs).summary()
+    st.update({"workload": "first %d requests of the seeded serving mix (Jacobi/Gauss-Seidel 1D-3D, T 10..500), "
+                           "Poisson arrivals at %.1f requests/s, %d slots, %.0f GB cap" % (n_requests, rate, slots,
+                                                                                          mem_cap / 1e9),
+               "rate_req_s": rate, "slots": slots})
+    return st
+
+
 def main():
     ap = argparse.ArgumentParser(description="serving benchmark (continuous batching vs plain one at a time)")
     ap.add_argument("--requests", type=int, default=200)

@@ -135,3 +135,38 @@ def test_batch_periodic_3d_full_size_equals_solo():
         torch.cuda.synchronize()
         assert torch.equal(u, v)
         st.close()
+
+
+def test_batch_periodic_3d_full_size_equals_oracle():
+    """The 512^3 periodic mix (Jacobi 7P, Jacobi 27P, Gauss-Seidel 7P) in one batch at T = 2, in the batch's
+    launch configuration, against the oracle on the whole grid, bit for bit."""
+    import ctypes
+    import torch
+    import oracle
+    from paper_2010_04868_gb300 import inputs
+    from paper_2010_04868_gb300 import stencil as S
+    ext = (512, 512, 512)
+    T = 2
+    specs = [(0, 7, S.STENCIL_JACOBI), (1, 27, S.STENCIL_JACOBI), (0, 7, S.STENCIL_GAUSS_SEIDEL)]
+    u0h = inputs.grid(inputs.SEED_BASE + 6, ext)
+    u0 = torch.from_numpy(u0h).cuda()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    sts, grids, us, scs, ws = [], [], [], [], []
+    for shape, k, method in specs:
+        w = list(inputs.normalized_weights(inputs.SEED_BASE + 210 + k + method, k))
+        st = S.Stencil(3, shape, 1, w, method, S.STENCIL_BC_PERIODIC)
+        u = u0.clone()
+        sc = torch.empty_like(u) if method == S.STENCIL_JACOBI else None
+        sts.append(st)
+        us.append(u)
+        scs.append(sc)
+        ws.append(w)
+        grids.append(st.grid(u, sc))
+    S.stencil_run_batch([s.handle for s in sts], grids, [T] * 3, stream)
+    torch.cuda.synchronize()
+    for st, u, w, (shape, k, method) in zip(sts, us, ws, specs):
+        assert st.status() == 0
+        ref = oracle.run(u0h, T, dim=3, shape=shape, r=1, weights=w, method=method, bc=1)
+        got = u.cpu().numpy()
+        assert bits_equal(got, ref), first_diff(got, ref)
+        st.close()

@@ -124,3 +124,16 @@ def test_programmatic_launches_replay_in_a_cuda_graph(dim, ext, kernel, tb, T):
         got = u.cpu().numpy()
         assert bits_equal(got, ref), first_diff(got, ref)
     st.close()
+
+
+@pytest.mark.parametrize("shape,k", [("star", 5), ("box", 9)])
+def test_jacobi2d_full_size_plain_equals_oracle_whole_grid(shape, k):
+    """The 4096^2 Jacobi workload's seeded grid and weights, plain per-step kernel in its launch configuration,
+    T = 3, against the oracle on every point."""
+    from paper_2010_04868_gb300 import inputs
+    ext = (4096, 4096)
+    w = inputs.normalized_weights(inputs.SEED_BASE + 100 + k, k)
+    u0 = inputs.grid(inputs.SEED_BASE + 2, ext)
+    ref = oracle_run(u0, 3, 2, shape, 1, w, "jacobi", "constant", 0.0, "fma")
+    got = gpu_run(u0, 3, 2, shape, 1, w, "jacobi", "constant", 0.0, "fma", plan=1)
+    assert bits_equal(got, ref), first_diff(got, ref)
