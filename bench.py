@@ -48,9 +48,10 @@ CSRC = os.path.join(PKG, "csrc")
 N_SIDE = 4096
 T_STEPS = 1000
 STENCILS = (("2d5p", 0, 5), ("2d9p", 1, 9))   # name, shape id, K
-KERNEL_NAMES = {1: "plain", 2: "blocked", 3: "wavefront", 4: "diamond"}
+KERNEL_NAMES = {1: "plain", 2: "blocked", 3: "wavefront", 4: "diamond", 5: "stream"}
 # the kernel source files each plan's code comes from (hashed to key the DRAM traffic table)
 PLAN_SOURCES = {"plain": ("k_plain.cu", "common.cuh"), "blocked": ("k_blocked.cu", "common.cuh"),
+                "stream": ("k_stream.cu", "common.cuh"),
                 "diamond": ("k_diamond.cu", "common.cuh"), "wavefront": ("k_wavefront.cu", "common.cuh"),
                 "batch": ("k_batch.cu", "k_plain.cu", "common.cuh")}
 FALLBACK_HBM_GBS = 6800.0   # the profiling recipe's fallback copy bandwidth, used only without a measured one
@@ -173,7 +174,7 @@ def job_value(updates_per_rank_step, world, ms_per_step):
 def passes_of(plan, T):
     """Passes over the grid through HBM: every step for the plain kernel, every T_b steps for the
     blocked and split-tiled kernels, every 32-sweep block for the wavefront."""
-    if plan["kernel"] in ("blocked", "diamond"):
+    if plan["kernel"] in ("blocked", "diamond", "stream"):
         return -(-T // max(1, plan["tb"]))
     if plan["kernel"] == "wavefront":
         return -(-T // 32)
@@ -401,6 +402,28 @@ def run_ours(args):
         plain[name] = round(N_SIDE * N_SIDE * T_STEPS / (e0.elapsed_time(e1) * 1e-3) / 1e9, 3)
         wk["st"].set_plan(S.STENCIL_KERNEL_AUTO)
 
+    # the streaming temporally blocked kernel (T_b = 2 and 4, default tiles) on the same grids
+    blocked = {}
+    for name, _, _ in STENCILS:
+        wk = work[name]
+        for tb in (2, 4):
+            wk["st"].set_plan(S.STENCIL_KERNEL_STREAM, tb)
+            wk["u"].copy_(u0)
+            wk["st"].run(wk["u"], 8, wk["scratch"])
+            wk["u"].copy_(u0)
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wk["st"].run(wk["u"], T_STEPS, wk["scratch"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            blocked["%s_tb%d" % (name, tb)] = round(N_SIDE * N_SIDE * T_STEPS / (e0.elapsed_time(e1) * 1e-3) / 1e9, 3)
+        wk["st"].set_plan(S.STENCIL_KERNEL_AUTO)
+        rc = wk["st"].status()
+        if rc != 0:
+            raise RuntimeError("device status after the streaming kernel: " + S.strerror(rc))
+
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(work, u0_host, stream, S)
@@ -424,7 +447,8 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 uniform [0,1), seeded normalised weights)",
             "config": workload_config(world),
-            "per_stencil_gstencil_s": per_stencil, "plain_kernel_gstencil_s": plain, "plans": plans,
+            "per_stencil_gstencil_s": per_stencil, "plain_kernel_gstencil_s": plain,
+            "stream_blocked_kernel_gstencil_s": blocked, "plans": plans,
             "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches),
             "e2e": e2e, "cpu_baseline": cpu, "method_configs": extra,
         }

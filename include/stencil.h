@@ -76,6 +76,8 @@ extern "C" {
 #define STENCIL_KERNEL_BLOCKED 2   /* Jacobi: tile + halo staged in shared memory, T_b steps per pass */
 #define STENCIL_KERNEL_WAVEFRONT 3 /* Gauss-Seidel: time-skewed wavefront, warp lanes hold sweeps */
 #define STENCIL_KERNEL_DIAMOND 4   /* Jacobi: split (diamond) temporal tiles, no redundant work, in place */
+#define STENCIL_KERNEL_STREAM 5    /* Jacobi 2D/3D: slowest axis streamed, one ring of planes per time
+                                      level in shared memory, T_b steps per pass */
 
 typedef struct stencil_handle_s* stencil_handle; /* opaque, owned by the library */
 
@@ -117,6 +119,20 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
  *            warps and a scheduler warp per tile); 0 = default.
  * A family that cannot run a given (method, boundary, grid) makes stencil_run
  * return EUNSUPPORTED.
+ *
+ * STREAM (Jacobi, 2D with radius 1 or 2, 3D with radius 1, constant weights)
+ * is temporal blocking without a tile along the slowest axis (Section 1's
+ * blocking methods; Section 3.4's tiles of T_b steps): a CTA owns a
+ * cross-section tile (tile[2] = W2 staged columns, a multiple of 32 up to
+ * 256; in 3D tile[1] = W1 staged rows) including a halo of T_b r per side,
+ * and a chunk of tile[0] rows (2D) or planes (3D) of the slowest axis, which
+ * it streams through shared memory: one ring of planes per time level, the
+ * input planes arriving by TMA (constant boundary) or cp.async (periodic)
+ * ahead of use, all T_b levels advancing behind one CTA barrier per group of
+ * planes, the last level written straight to the output. HBM is read and
+ * written once per T_b steps; only the cross-section halo is computed
+ * twice. tb = T_b (1..4 in 2D with radius 1, else 1..2; larger values are
+ * lowered); T mod T_b steps run as plain steps. 0 = default.
  *
  * DIAMOND (Jacobi) is the diamond temporal tiling of Section 3.4 in split
  * form on every axis: each axis is cut into periods of an A segment (a

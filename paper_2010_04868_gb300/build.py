@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgb300stencil.so")
-SOURCES = ["abi.cu", "k_plain.cu", "k_blocked.cu", "k_diamond.cu", "k_wavefront.cu", "tune.cu", "k_noalloc.cu", "k_batch.cu", "k_life.cu", "k_lcs.cu"]
+SOURCES = ["abi.cu", "k_plain.cu", "k_blocked.cu", "k_stream.cu", "k_diamond.cu", "k_wavefront.cu", "tune.cu", "k_noalloc.cu", "k_batch.cu", "k_life.cu", "k_lcs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fno-strict-aliasing", "-I", os.path.join(ROOT, "include")]

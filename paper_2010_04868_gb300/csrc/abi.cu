@@ -122,8 +122,9 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
 
 int stencil_set_plan(stencil_handle h, int kernel, int tb, const int64_t tile[3])
 {
-    if (!h || kernel < STENCIL_KERNEL_AUTO || kernel > STENCIL_KERNEL_DIAMOND || tb < 0) return STENCIL_EINVAL;
-    if ((kernel == STENCIL_KERNEL_BLOCKED || kernel == STENCIL_KERNEL_DIAMOND) && h->method != STENCIL_JACOBI)
+    if (!h || kernel < STENCIL_KERNEL_AUTO || kernel > STENCIL_KERNEL_STREAM || tb < 0) return STENCIL_EINVAL;
+    if ((kernel == STENCIL_KERNEL_BLOCKED || kernel == STENCIL_KERNEL_DIAMOND || kernel == STENCIL_KERNEL_STREAM) &&
+        h->method != STENCIL_JACOBI)
         return STENCIL_EINVAL;
     if (kernel == STENCIL_KERNEL_WAVEFRONT && (h->method != STENCIL_GAUSS_SEIDEL || tb > 32)) return STENCIL_EINVAL;
     h->plan_kernel = kernel;
@@ -221,6 +222,11 @@ int stencil_run(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_s
             rc = STENCIL_EUNSUPPORTED;
         else
             rc = jacobi_blocked_run(ctx, g->data, scratch, T, p.tb, p.tile);
+    } else if (p.kernel == STENCIL_KERNEL_STREAM) {
+        if (!jacobi_stream_supported(h, ctx.g))
+            rc = STENCIL_EUNSUPPORTED;
+        else
+            rc = jacobi_stream_run(ctx, g->data, scratch, T, p.tb, p.tile);
     } else {
         double* a = g->data;
         double* b = scratch;

@@ -93,6 +93,12 @@ int gs_plain_run(const RunCtx& ctx, double* u, int64_t T);
 int jacobi_blocked_run(const RunCtx& ctx, double* a, double* b, int64_t T, int tb, const int64_t tile[3]);
 bool jacobi_blocked_supported(const stencil_handle_s* h, const Geo& g);
 
+// Streaming temporally blocked Jacobi (2D/3D): T steps from a (=g.data) using b
+// (=scratch), passes of tb steps; the result ends in a. EUNSUPPORTED if the
+// configuration is not covered.
+int jacobi_stream_run(const RunCtx& ctx, double* a, double* b, int64_t T, int tb, const int64_t tile[3]);
+bool jacobi_stream_supported(const stencil_handle_s* h, const Geo& g);
+
 // Split-tiled (diamond) Jacobi: T steps in place on u, bands of H steps,
 // periods of tile[d] points per axis (0 = defaults). Returns EUNSUPPORTED if
 // the configuration or the grid is not covered.

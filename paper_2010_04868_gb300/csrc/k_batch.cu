@@ -21,8 +21,9 @@
 // stencils run the same compile-time specialised code as the single-problem
 // kernels; other stencils use run-time offset tables. The tiles and depths
 // T_b come from each problem's tuned plan. Gauss-Seidel problems whose plan
-// is the wavefront kernel, and stencils with more than 125 points, run as
-// their own launches on the same stream. The whole enqueue is captured once
+// is the wavefront kernel, Jacobi problems whose plan is the streaming blocked
+// kernel, and stencils with more than 125 points, run as their own launches
+// on the same stream. The whole enqueue is captured once
 // into a CUDA graph, cached on the batch's shape (handles, pointers, extents,
 // step counts, plans) and replayed afterwards. Every point is computed with
 // the same descending-order sum and rounding as the single-problem kernels,
@@ -599,8 +600,12 @@ int batch_run(const stencil_handle* hs, const stencil_grid* gs, const int64_t* T
         const bool wave = h->method == GAUSS_SEIDEL && h->bc == BC_CONSTANT &&
                           plans[i].kernel == STENCIL_KERNEL_WAVEFRONT &&
                           gs_wavefront_supported(h, make_geo(h->dim, gs[i].ext));
-        // per-point weights: the problem runs as its own launches (the shared kernel reads constant weights)
-        if (!wave && !h->field && h->K <= BMAXK && describe(h, &gs[i], Ts[i], plans[i], P)) {
+        // the streaming blocked Jacobi plan keeps its own kernel (its passes need no workspace, so they
+        // are captured with the rest); per-point weights: the problem runs as its own launches (the shared
+        // kernel reads constant weights)
+        const bool stream = h->method == JACOBI && plans[i].kernel == STENCIL_KERNEL_STREAM &&
+                            jacobi_stream_supported(h, make_geo(h->dim, gs[i].ext));
+        if (!wave && !stream && !h->field && h->K <= BMAXK && describe(h, &gs[i], Ts[i], plans[i], P)) {
             P.spec = spec_of(h);
             if (P.kind == BK_GSTILE && h->dim == 1) P.spec = SP_NONE;
             inside.push_back(i);

@@ -3,9 +3,10 @@
 // The paper picks blocking sizes by trying every power-of-two, symmetric
 // size and keeping the fastest (Section 4.1), and leaves an auto-tuner to
 // future work (Section 6). Here the tuner measures instead of guessing:
-//   * Jacobi: the plain per-step kernel, the temporally blocked kernel over a
-//     small set of tiles and depths T_b, and the split (diamond) tiles over a
-//     few periods and band heights are each timed for a few steps on private
+//   * Jacobi: the plain per-step kernel, the temporally blocked kernels (the
+//     overlapped tiles, and in 2D/3D the streaming tiles) over a small set of
+//     tiles and depths T_b, and the split (diamond) tiles over a few periods
+//     and band heights are each timed for a few steps on private
 //     buffers of the run's extents; the fastest per step wins, a plan other
 //     than plain only if it is more than 3% faster. On GB300 the FP64 pipe, not HBM, bounds large grids, so the plain
 //     kernel usually wins there and blocking wins where launches dominate.
@@ -118,6 +119,21 @@ std::vector<Plan> jacobi_candidates(const stencil_handle_s* h, const Geo& g, int
             dia(16, 0, 88, 88);
         }
     }
+    // streaming blocked tiles (2D/3D): the slowest axis streamed, redundancy on the cross-section only
+    if (jacobi_stream_supported(h, g)) {
+        auto st = [&](int tb, int64_t w1, int64_t w2) {
+            if (tb <= T) c.push_back(Plan{STENCIL_KERNEL_STREAM, tb, {0, w1, w2}});
+        };
+        if (h->dim == 2) {
+            for (int tb : {1, 2, 4}) st(tb, 0, 256);
+            st(2, 0, 192);
+            if (h->r == 1) st(3, 0, 256);
+        } else {
+            st(1, 16, 64);
+            st(1, 24, 128);
+            st(2, 12, 64);
+        }
+    }
     if (!jacobi_blocked_supported(h, g)) return c;
     auto add = [&](int tb, int64_t t0, int64_t t1, int64_t t2) {
         if (tb <= T) c.push_back(Plan{STENCIL_KERNEL_BLOCKED, tb, {t0, t1, t2}});
@@ -208,7 +224,7 @@ Plan plan_for(const stencil_handle_s* hc, const Geo& g, int64_t T, cudaStream_t 
         return default_plan(h, g);
     }
     if (getenv("STENCIL_NO_TUNE")) return default_plan(h, g);
-    if (!jacobi_blocked_supported(h, g) && !jacobi_diamond_supported(h, g))
+    if (!jacobi_blocked_supported(h, g) && !jacobi_diamond_supported(h, g) && !jacobi_stream_supported(h, g))
         return default_plan(h, g);  // the plain kernel is the only candidate
     const size_t n = (size_t)(g.n0 * g.n1 * g.n2);
     double *a = nullptr, *b = nullptr;

@@ -206,6 +206,7 @@ int main(int argc, char** argv)
         add_shapes<8>(shapes, true);
         add_shapes<16>(shapes, true);
     } else {
+        add_shapes<2>(shapes, false);
         add_shapes<4>(shapes, false);
         add_shapes<8>(shapes, false);
     }

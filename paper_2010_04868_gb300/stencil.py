@@ -25,6 +25,7 @@ STENCIL_BC_CONSTANT, STENCIL_BC_PERIODIC = 0, 1
 STENCIL_ARITH_FMA, STENCIL_ARITH_UNFUSED = 0, 1
 STENCIL_KERNEL_AUTO, STENCIL_KERNEL_PLAIN, STENCIL_KERNEL_BLOCKED, STENCIL_KERNEL_WAVEFRONT = 0, 1, 2, 3
 STENCIL_KERNEL_DIAMOND = 4
+STENCIL_KERNEL_STREAM = 5
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgb300stencil.so")
 

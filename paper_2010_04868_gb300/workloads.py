@@ -1,6 +1,6 @@
 """The benchmark workloads, runnable one at a time with a chosen kernel family.
 
-    python -m paper_2010_04868_gb300.workloads --config NAME [--kernel auto|plain|blocked|wavefront|diamond]
+    python -m paper_2010_04868_gb300.workloads --config NAME [--kernel auto|plain|blocked|wavefront|diamond|stream]
                                                [--T STEPS] [--reps N] [--tb TB] [--tile A,B,C]
                                                [--ext E0,E1,...]
 
@@ -73,7 +73,7 @@ FIELD = {"jacobi2d5v", "gs2d5v", "gs1d3v", "jacobi3d7v"}
 
 RADIUS = {"jacobi1d5": 2, "jacobi2d9s": 2, "jacobi3d13": 2, "gs2d9s": 2}
 
-KERNELS = {"auto": 0, "plain": 1, "blocked": 2, "wavefront": 3, "diamond": 4}
+KERNELS = {"auto": 0, "plain": 1, "blocked": 2, "wavefront": 3, "diamond": 4, "stream": 5}
 
 
 def k_points(dim, shape, r=1):
