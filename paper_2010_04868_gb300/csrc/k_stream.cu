@@ -9,8 +9,8 @@
 // of Z rows/planes of the streamed axis. It keeps, for every time level
 // s = 0 .. T_b - 1, a ring of planes in shared memory and advances all levels
 // in one pass along the streamed axis:
-//   iteration it: level 0 (the input) receives M planes by TMA (issued one
-//   iteration ahead), and each level s >= 1 computes M planes from the
+//   iteration it: level 0 (the input) receives M planes by TMA (issued two
+//   iterations ahead), and each level s >= 1 computes M planes from the
 //   planes level s - 1 finished in earlier iterations; level T_b writes its
 //   planes straight to the output grid. One CTA barrier per iteration.
 // Level s trails level s - 1 by M + r planes, so every value a level reads was
@@ -102,8 +102,12 @@ __device__ __forceinline__ int ring_mod(int a, int c)
 }
 
 
+// Input planes are requested this many iterations before the iteration that waits for them.
+constexpr int STREAM_PF = 2;
+
 // Level-0 load of planes [c0 + j M, + M) into ring slots (j M) mod C0 ...: by TMA (thread 0,
-// mbarrier j & 1) or by cp.async from wrapped / checked coordinates (every thread, its own cells).
+// mbarrier j mod (STREAM_PF + 1)) or by cp.async from wrapped / checked coordinates (every
+// thread, its own cells).
 template <int DIM, int M>
 __device__ __forceinline__ void stream_load(const CUtensorMap* tmap, const double* __restrict__ in, const Geo& g,
                                             int bc, double c, const StrGeo& sg, double* ring0, uint32_t bar_base,
@@ -114,7 +118,7 @@ __device__ __forceinline__ void stream_load(const CUtensorMap* tmap, const doubl
     const int64_t z = c0 + (int64_t)j * M;
     if (sg.use_tma) {
         if (threadIdx.x == 0 && threadIdx.y == 0) {
-            const uint32_t bar = bar_base + 8u * (uint32_t)(j & 1);
+            const uint32_t bar = bar_base + 8u * (uint32_t)(j % (STREAM_PF + 1));
             const uint32_t bytes = (uint32_t)(M * P * 8);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_stream(const __grid_constant_
     constexpr int K = S::K;
     constexpr int ZA = DIM == 2 ? 1 : 0;  // the streamed axis among Stn's three offset components
     extern __shared__ __align__(128) double sm[];
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t bars[STREAM_PF + 1];
     const int P = sg.W1 * sg.W2;
     double* ring[TB];
     ring[0] = sm;
@@ -200,8 +204,8 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_stream(const __grid_constant_
     const bool constant = bc == BC_CONSTANT;
     const uint32_t bar_base = s_u32(&bars[0]);
     if (sg.use_tma && threadIdx.x == 0 && threadIdx.y == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_base) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_base + 8u) : "memory");
+        for (int i = 0; i <= STREAM_PF; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_base + 8u * i) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // cells outside the grid hold c in every plane of the rings of levels 1 .. TB - 1
@@ -216,22 +220,26 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_stream(const __grid_constant_
     __syncthreads();
     griddep_wait();  // launched programmatically: the previous pass has finished writing its output
 
-    stream_load<DIM, M>(&tmap, in, g, bc, c, sg, ring[0], bar_base, c0, 0, gj0, gx0, jb);
-    if (!sg.use_tma) asm volatile("cp.async.commit_group;" ::: "memory");
+    // the first STREAM_PF loads (one cp.async group each, possibly empty)
+    for (int j = 0; j < STREAM_PF; ++j) {
+        if (j < niter && c0 + (int64_t)j * M < hi0)
+            stream_load<DIM, M>(&tmap, in, g, bc, c, sg, ring[0], bar_base, c0, j, gj0, gx0, jb);
+        if (!sg.use_tma) asm volatile("cp.async.commit_group;" ::: "memory");
+    }
 
     for (int it = 0; it < niter; ++it) {
-        // (a) the load of level-0 planes for iteration it + 1; its slots were last read before the
-        //     previous barrier
-        if (it + 1 < niter && c0 + (int64_t)(it + 1) * M < hi0)
-            stream_load<DIM, M>(&tmap, in, g, bc, c, sg, ring[0], bar_base, c0, it + 1, gj0, gx0, jb);
+        // (a) the load of level-0 planes for iteration it + STREAM_PF; its slots were last read
+        //     before the previous barrier
+        if (it + STREAM_PF < niter && c0 + (int64_t)(it + STREAM_PF) * M < hi0)
+            stream_load<DIM, M>(&tmap, in, g, bc, c, sg, ring[0], bar_base, c0, it + STREAM_PF, gj0, gx0, jb);
         // (b) the planes loaded for iteration it are complete (and set to c where outside the grid);
         //     they are first read in iteration it + 1, after the barrier below
         if (!sg.use_tma) {
             asm volatile("cp.async.commit_group;" ::: "memory");
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
+            asm volatile("cp.async.wait_group %0;" ::"n"(STREAM_PF) : "memory");
         } else if (c0 + (int64_t)it * M < hi0) {
-            const uint32_t bar = bar_base + 8u * (uint32_t)(it & 1);
-            const uint32_t par = (uint32_t)((it >> 1) & 1);
+            const uint32_t bar = bar_base + 8u * (uint32_t)(it % (STREAM_PF + 1));
+            const uint32_t par = (uint32_t)((it / (STREAM_PF + 1)) & 1);
             if (!mbar_wait_parity(bar, par)) {
                 if (x == 0 && threadIdx.y == 0) atomicExch(status, DEV_TIMEOUT);
                 mbar_wait_parity_backoff(bar, par);
@@ -405,20 +413,20 @@ static size_t make_str(const stencil_handle_s* h, const Geo& g, int tb, const in
         sg.J = 1;
         block = dim3(sg.W2, 1, 1);
     }
-    sg.C0 = (3 * M + 2 * r + M - 1) / M * M;
+    sg.C0 = ((STREAM_PF + 2) * M + 2 * r + M - 1) / M * M;
     sg.C = 2 * M + 2 * r;
     sg.ns2 = (int)((g.n2 + sg.B2 - 1) / sg.B2);
     sg.ns1 = dim == 3 ? (int)((n1 + sg.B1 - 1) / sg.B1) : 1;
     int64_t Z = tile && tile[0] > 0 ? tile[0] : 0;
     if (Z <= 0) {
-        // chunks so that the CTAs fill whole waves of the SMs (2 resident CTAs each)
+        // about 8 CTAs per SM, so that the last wave of every pass is a small part of it
         int nsm = 152, dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         const int64_t tiles = (int64_t)sg.ns1 * sg.ns2;
-        int64_t want = (2 * (int64_t)nsm + tiles - 1) / tiles;
-        while (want > 1 && (nz + want - 1) / want < 8 * M) --want;
+        const int64_t want = (8 * (int64_t)nsm + tiles - 1) / tiles;
         Z = (nz + want - 1) / want;
+        if (Z < 2 * M) Z = 2 * M;
     }
     if (Z > nz) Z = nz;
     sg.Z = (int)Z;

@@ -103,3 +103,37 @@ def cells(seed: int, ext, density: float = 0.5) -> np.ndarray:
 def sequence(seed: int, n: int, sigma: int = 4) -> np.ndarray:
     """A uint8 sequence of n symbols drawn uniformly from {0, .., sigma - 1} (SplitMix64 modulo sigma)."""
     return (splitmix64(seed, 0, int(n)) % np.uint64(sigma)).astype(np.uint8)
+
+
+def _i64(v: int) -> int:
+    """A 64-bit pattern as a signed int64 value (two's complement)."""
+    v &= 0xFFFFFFFFFFFFFFFF
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def grid_into(out, seed: int, chunk: int = 1 << 22):
+    """Fill a float64 torch tensor (any device, contiguous) with the same values as grid(seed, out.shape).
+
+    The same SplitMix64 stream, evaluated in torch int64 arithmetic (additions and products wrap
+    modulo 2**64; a logical right shift is an arithmetic shift with the sign-extended bits masked
+    off), a chunk of elements at a time so that temporaries stay small.
+    """
+    import torch
+    flat = out.view(-1)
+    n = flat.numel()
+    g, m1, m2, s = _i64(0x9E3779B97F4A7C15), _i64(0xBF58476D1CE4E5B9), _i64(0x94D049BB133111EB), _i64(seed)
+
+    def srl(x, k):
+        return (x >> k) & ((1 << (64 - k)) - 1)
+
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        z = torch.arange(a + 1, b + 1, dtype=torch.int64, device=flat.device) * g + s
+        z = z ^ srl(z, 30)
+        z = z * m1
+        z = z ^ srl(z, 27)
+        z = z * m2
+        z = z ^ srl(z, 31)
+        flat[a:b] = srl(z, 11).to(torch.float64) * _TWO_M53
+    return out
+

@@ -1,7 +1,7 @@
 """CPU restatement of the streaming temporally blocked Jacobi kernel (csrc/k_stream.cu).
 
 The emulation follows the kernel's geometry choice (make_str), its iteration structure (level-0
-planes loaded one iteration ahead, every level advancing M planes per iteration behind one
+planes requested two iterations ahead, every level advancing M planes per iteration behind one
 barrier), its ring slots and its per-level validity rules. Every ring cell carries a tag (level,
 plane, iteration written); each read checks that it finds the plane it needs, written before the
 last barrier and not yet overwritten, and that every index stays inside its ring. Every output
@@ -27,6 +27,9 @@ def canonical_offsets(dim, shape, r):
                     continue
                 offs.append((a, b, c))
     return offs
+
+
+PF = 2   # iterations between requesting input planes and waiting for them
 
 
 def stream_m(dim):
@@ -61,17 +64,16 @@ def make_str(dim, r, ext, tb, tile=(0, 0, 0), nsm=152):
         B1, J, block = W1 - 2 * h, W1 // jg, (W2, jg)
     else:
         W1, B1, J, block = 1, 1, 1, (W2, 1)
-    C0 = (3 * M + 2 * r + M - 1) // M * M
+    C0 = ((PF + 2) * M + 2 * r + M - 1) // M * M
     C = 2 * M + 2 * r
     ns2 = (n2 + B2 - 1) // B2
     ns1 = (n1x + B1 - 1) // B1 if dim == 3 else 1
     Z = tile[0] if tile[0] > 0 else 0
     if Z <= 0:
         tiles = ns1 * ns2
-        want = (2 * nsm + tiles - 1) // tiles
-        while want > 1 and (nz + want - 1) // want < 8 * M:
-            want -= 1
+        want = (8 * nsm + tiles - 1) // tiles
         Z = (nz + want - 1) // want
+        Z = max(Z, 2 * M)
     Z = min(Z, nz)
     nchunk = (nz + Z - 1) // Z
     planes = C0 + (tb - 1) * C
@@ -133,12 +135,14 @@ def emulate(u0, dim, shape, r, w, bc, c, tb, tile=(0, 0, 0), tma=True):
                 rings[0][slot + m] = vals
                 tag_row[0][slot + m] = z
                 tag_ready[0][slot + m] = j + 1
-            assert it_issue == j - 1
+            assert it_issue == j - PF
 
-        load(0, -1)
+        for j in range(PF):
+            if j < niter and c0 + j * M < hi0:
+                load(j, j - PF)
         for it in range(niter):
-            if it + 1 < niter and c0 + (it + 1) * M < hi0:
-                load(it + 1, it)
+            if it + PF < niter and c0 + (it + PF) * M < hi0:
+                load(it + PF, it)
             for s in range(1, tb + 1):
                 cs = c0 - s * (M + r)
                 y0 = cs + it * M
@@ -242,7 +246,7 @@ def test_stream_schedule_and_result(dim, shape, r, ext, bc, c, tb, tile):
 
 
 def test_default_geometry_of_the_4096_grid():
-    """The default plan on the 4096^2 workload: 256-column strips, chunks filling two CTAs per SM."""
+    """The default plan on the 4096^2 workload: 256-column strips, chunks for about 8 CTAs per SM."""
     sg = make_str(2, 1, (4096, 4096), 2)
     assert sg["W2"] == 256 and sg["B2"] == 252 and sg["ns2"] == 17
-    assert sg["ns2"] * sg["nchunk"] >= 2 * 152 and sg["smem"] <= 227 * 1024
+    assert sg["ns2"] * sg["nchunk"] >= 8 * 152 and sg["smem"] <= 227 * 1024

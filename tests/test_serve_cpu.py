@@ -1,5 +1,7 @@
-"""Scheduler of the serving loop, driven by a simulated executor (no GPU)."""
-from paper_2010_04868_gb300 import serve
+"""Scheduler and arena of the serving loop, driven by a simulated executor (no GPU)."""
+import numpy as np
+
+from paper_2010_04868_gb300 import inputs, serve
 
 
 def test_request_mix_follows_the_recipe():
@@ -7,6 +9,7 @@ def test_request_mix_follows_the_recipe():
     assert len(reqs) == 400
     for r in reqs:
         assert r.dim in (1, 2, 3) and 10 <= r.T <= 500
+        assert r.cls in serve.CLASSES
         if r.method == 1:
             assert r.shape == 0
         if r.dim == 1:
@@ -19,6 +22,48 @@ def test_request_mix_follows_the_recipe():
     assert serve.request_mix(50)[7] == serve.request_mix(50)[7]   # deterministic
 
 
+def test_catalog_weights_are_normalised_and_distinct():
+    seen = set()
+    for c in serve.CLASSES:
+        w = serve.class_weights(c)
+        k = 2 * c[1] + 1 if c[2] == 0 else 3 ** c[1]
+        assert len(w) == k and (w > 0).all() and abs(w.sum() - 1) < 1e-12
+        seen.add(tuple(w))
+    assert len(seen) == len(serve.CLASSES)
+
+
+def test_arena_blocks_never_overlap_and_coalesce():
+    """Random allocations and releases against a byte map: aligned, disjoint, inside the cap, and the
+    free list returns to one block when everything is released."""
+    cap = 1 << 20
+    a = serve.ArenaBlocks(cap)
+    owner = np.zeros(cap // serve.ALIGN, dtype=np.int64)
+    live = {}
+    u = inputs.uniform(77, 4000)
+    for i in range(2000):
+        if live and u[2 * i] < 0.45:
+            k = sorted(live)[int(u[2 * i + 1] * len(live))]
+            off, n = live.pop(k)
+            a.release(off, n)
+            owner[off // serve.ALIGN:(off + n + serve.ALIGN - 1) // serve.ALIGN] = 0
+        else:
+            n = 1 + int(u[2 * i + 1] * 60000)
+            off = a.alloc(n)
+            if off is None:
+                continue
+            assert off % serve.ALIGN == 0 and off + n <= cap
+            blk = owner[off // serve.ALIGN:(off + n + serve.ALIGN - 1) // serve.ALIGN]
+            assert (blk == 0).all(), "overlap"
+            blk[:] = i + 1
+            live[i] = (off, n)
+        assert a.used == sum((n + serve.ALIGN - 1) // serve.ALIGN * serve.ALIGN for _, n in live.values())
+        for (o1, l1), (o2, l2) in zip(a.free, a.free[1:]):
+            assert o1 + l1 < o2                               # sorted, disjoint, coalesced
+    for off, n in live.values():
+        a.release(off, n)
+    assert a.free == [(0, cap)] and a.used == 0
+
+
 def test_admission_respects_slots_memory_and_fifo():
     reqs = serve.request_mix(60)
     serve.poisson_arrivals(reqs, rate=2000.0)
@@ -29,9 +74,21 @@ def test_admission_respects_slots_memory_and_fifo():
     assert st.completed + st.rejected == len(reqs)
     assert st.rejected == too_big
     assert st.max_mem <= cap
-    assert ex.max_inflight <= 4
+    assert ex.max_inflight <= 4 and ex.slots_seen <= {0, 1, 2, 3}
     assert len(st.latencies_ms) == st.completed
     assert min(st.latencies_ms) >= 0.0
+
+
+def test_service_model_fit_and_stratified_sample():
+    reqs = serve.request_mix(300)
+    sample = serve.stratified_sample(reqs, 4)
+    assert {r.cls for r in sample} == {r.cls for r in reqs}
+    assert all(sum(1 for r in sample if r.cls == c) <= 4 for c in serve.CLASSES)
+    secs = [0.01 + 2e-9 * r.updates * (1 + r.method) for r in sample]
+    model = serve.fit_service_model(sample, secs)
+    for r, s in zip(sample, secs):
+        a, b = model[r.cls]
+        assert abs(a + b * r.updates - s) < 1e-9 * max(1.0, s) + 1e-12
 
 
 def test_one_at_a_time_queue_model():
