@@ -195,6 +195,7 @@ int stencil_run(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_s
         Plan p = plan_for(h, ctx.g, T, ctx.st);
         if (p.kernel == STENCIL_KERNEL_WAVEFRONT) {
             if (!gs_wavefront_supported(h, ctx.g)) return STENCIL_EUNSUPPORTED;
+            for (int d = 0; d < 3; ++d) ctx.wtile[d] = p.tile[d];
             return gs_wavefront_run(ctx, g->data, T, p.tb);
         }
         return gs_plain_run(ctx, g->data, T);

@@ -51,6 +51,8 @@ struct RunCtx {
     Geo g;
     cudaStream_t st;
     StencilDev sd;
+    // wavefront Gauss-Seidel parameters of the run's plan (tile[] of a WAVEFRONT plan, 0 = default)
+    int64_t wtile[3] = {0, 0, 0};
 };
 
 inline int cuda_rc(cudaError_t e) { return e == cudaSuccess ? STENCIL_OK : STENCIL_ECUDA; }
@@ -107,8 +109,8 @@ bool jacobi_diamond_supported(const stencil_handle_s* h, const Geo& g);
 
 // Time-skewed wavefront Gauss-Seidel: T sweeps in place.
 int gs_wavefront_run(const RunCtx& ctx, double* u, int64_t T, int lanes);
-// Size the handle's wavefront workspace for (g, T) ahead of a captured run.
-int gs_wavefront_prepare(stencil_handle_s* h, const Geo& g, int64_t T);
+// Size the handle's wavefront workspace for (g, T) and the plan's parameters ahead of a captured run.
+int gs_wavefront_prepare(stencil_handle_s* h, const Geo& g, int64_t T, const int64_t wtile[3]);
 bool gs_wavefront_supported(const stencil_handle_s* h, const Geo& g);
 
 // Geometry from a stencil_grid (padded to three dimensions).

@@ -676,7 +676,7 @@ int batch_run(const stencil_handle* hs, const stencil_grid* gs, const int64_t* T
     for (int i : outside) {
         stencil_handle_s* h = hs[i];
         if (h->method == GAUSS_SEIDEL && plans[i].kernel == STENCIL_KERNEL_WAVEFRONT) {
-            int rc = gs_wavefront_prepare(h, make_geo(h->dim, gs[i].ext), Ts[i]);
+            int rc = gs_wavefront_prepare(h, make_geo(h->dim, gs[i].ext), Ts[i], plans[i].tile);
             if (rc) return rc;
         }
     }

@@ -1034,8 +1034,8 @@ static int wave_tiles(const RunCtx& ctx, double* u, int64_t T, int lanes, bool p
         wg.a1 = box ? R : 0;
         wg.b1 = R * (1 + wg.a1);
         wg.a2 = wg.c2 = wg.b2 = 0;
-        // skewed rows per tile: 16, or what a fixed wavefront plan asks for (tile[1], 2..64)
-        const int64_t hp = h->plan_kernel == STENCIL_KERNEL_WAVEFRONT ? h->plan_tile[1] : 0;
+        // skewed rows per tile: 16, or what the wavefront plan asks for (tile[1], 2..64)
+        const int64_t hp = ctx.wtile[1];
         wg.H = hp >= 2 && hp <= 64 ? (int)hp : 16;
         wg.HJ = 1;
     } else {
@@ -1117,7 +1117,7 @@ static int launch_wave(const RunCtx& ctx, double* u, const WS& w, const WaveGeo&
     // two CTAs (8 worker warps) per SM by default: more tiles in flight would slow the tiles on
     // the DAG's critical path (they share the FP64 pipe); fewer leave it idle. A fixed wavefront
     // plan may ask for another count (tile[0]).
-    const int want = h->plan_kernel == STENCIL_KERNEL_WAVEFRONT && h->plan_tile[0] > 0 ? (int)h->plan_tile[0] : 2;
+    const int want = ctx.wtile[0] > 0 ? (int)ctx.wtile[0] : 2;
     int64_t nblk = (int64_t)nsm * (per_sm > want ? want : (per_sm > 0 ? per_sm : 1));
     const int64_t need = (wg.ntiles + 3) / 4;
     if (nblk > need) nblk = need;
@@ -1143,8 +1143,8 @@ static int launch_gs2d_dec(const RunCtx& ctx, double* u, const WaveGeo& wg, cons
         return STENCIL_ECUDA;
     }
     // every CTA waits on tiles other CTAs hold: all of them must be resident (the count is capped
-    // at the occupancy); 2 per SM by default, or what a fixed wavefront plan asks for (tile[0])
-    const int want = h->plan_kernel == STENCIL_KERNEL_WAVEFRONT && h->plan_tile[0] > 0 ? (int)h->plan_tile[0] : 2;
+    // at the occupancy); 2 per SM by default, or what the wavefront plan asks for (tile[0])
+    const int want = ctx.wtile[0] > 0 ? (int)ctx.wtile[0] : 2;
     int64_t nblk = (int64_t)nsm * (per_sm < want ? per_sm : want);
     if (nblk > wg.ntiles) nblk = wg.ntiles;
     const WaitCfg wc = take_wait_cfg(h);
@@ -1238,10 +1238,10 @@ static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, boo
         return STENCIL_EUNSUPPORTED;
     }
     if (h->dim == 2) {
-        // points per lane and step: 16, or 8 when a fixed wavefront plan asks for it (tile[2] = 8);
+        // points per lane and step: 16, or 8 when the wavefront plan asks for it (tile[2] = 8);
         // tile[2] = 1 selects the decoupled tile for the 5-point star with one weight per term
         // (measured level with the one-warp tile at best, so not the default)
-        const int64_t pw = h->plan_kernel == STENCIL_KERNEL_WAVEFRONT ? h->plan_tile[2] : 0;
+        const int64_t pw = ctx.wtile[2];
         const bool w8 = pw == 8;
         if (h->shape == STAR && h->r == 1)
             return w8 ? wave_tiles<2, STAR, 1, 8>(ctx, u, T, lanes, prep)
@@ -1263,7 +1263,7 @@ int gs_wavefront_run(const RunCtx& ctx, double* u, int64_t T, int lanes)
     return wave_dispatch(ctx, u, T, lanes, false);
 }
 
-int gs_wavefront_prepare(stencil_handle_s* h, const Geo& g, int64_t T)
+int gs_wavefront_prepare(stencil_handle_s* h, const Geo& g, int64_t T, const int64_t wtile[3])
 {
     if (!gs_wavefront_supported(h, g) || T <= 0) return STENCIL_OK;
     RunCtx ctx;
@@ -1271,6 +1271,7 @@ int gs_wavefront_prepare(stencil_handle_s* h, const Geo& g, int64_t T)
     ctx.g = g;
     ctx.st = 0;
     ctx.sd = make_sd(h, g.n0 * g.n1 * g.n2);
+    for (int d = 0; d < 3; ++d) ctx.wtile[d] = wtile ? wtile[d] : 0;
     return wave_dispatch(ctx, nullptr, T, 0, true);
 }
 

@@ -12,7 +12,11 @@
 //     kernel usually wins there and blocking wins where launches dominate.
 //   * Gauss-Seidel: the wavefront kernel whenever it is legal (constant
 //     boundary); it was faster than per-sweep execution in every measured
-//     case by one to two orders of magnitude, so it is not re-timed.
+//     case by one to two orders of magnitude, so the plain sweep is not
+//     timed. In 2D and 3D its parameters are: CTAs per SM of the persistent
+//     kernel (tile[0]), skewed rows per tile (tile[1], 2D) and points per
+//     lane and step or the decoupled tile (tile[2], 2D radius 1); a few
+//     combinations around the default are timed like the Jacobi plans.
 // Results are cached per (stencil, extent class, T class) in memory and, when
 // the environment variable STENCIL_TUNE_CACHE names a file, in that file (one
 // JSON object per line). A run inside CUDA stream capture never tunes; it
@@ -162,6 +166,27 @@ std::vector<Plan> jacobi_candidates(const stencil_handle_s* h, const Geo& g, int
     return c;
 }
 
+// Wavefront Gauss-Seidel parameter sets (the first is the default, the reference).
+std::vector<Plan> gs_candidates(const stencil_handle_s* h)
+{
+    std::vector<Plan> c;
+    auto add = [&](int64_t ctas, int64_t rows, int64_t pts) {
+        c.push_back(Plan{STENCIL_KERNEL_WAVEFRONT, 0, {ctas, rows, pts}});
+    };
+    add(0, 0, 0);
+    if (h->dim == 2) {
+        add(3, 16, 16);
+        add(4, 16, 16);
+        add(3, 8, 16);
+        if (h->r == 1) add(2, 32, 8);
+        if (h->r == 1 && h->shape == STAR && !h->field) add(3, 32, 1);   // the decoupled tile
+    } else {
+        add(3, 0, 0);
+        add(4, 0, 0);
+    }
+    return c;
+}
+
 // Time one candidate: ms per time step over probe steps (after one warm-up).
 double time_candidate(stencil_handle_s* h, const Plan& p, double* a, double* b, const int64_t ext[3], int64_t probe,
                       cudaStream_t st)
@@ -208,7 +233,9 @@ Plan plan_for(const stencil_handle_s* hc, const Geo& g, int64_t T, cudaStream_t 
         Plan p{h->plan_kernel, h->plan_tb, {h->plan_tile[0], h->plan_tile[1], h->plan_tile[2]}};
         return p;
     }
-    if (h->method == GAUSS_SEIDEL) return default_plan(h, g);
+    const bool gs_tuned = h->method == GAUSS_SEIDEL && h->dim >= 2 && h->bc == BC_CONSTANT &&
+                          gs_wavefront_supported(h, g);
+    if (h->method == GAUSS_SEIDEL && !gs_tuned) return default_plan(h, g);
     const std::string key = plan_key(h, g, T);
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -224,7 +251,8 @@ Plan plan_for(const stencil_handle_s* hc, const Geo& g, int64_t T, cudaStream_t 
         return default_plan(h, g);
     }
     if (getenv("STENCIL_NO_TUNE")) return default_plan(h, g);
-    if (!jacobi_blocked_supported(h, g) && !jacobi_diamond_supported(h, g) && !jacobi_stream_supported(h, g))
+    if (!gs_tuned && !jacobi_blocked_supported(h, g) && !jacobi_diamond_supported(h, g) &&
+        !jacobi_stream_supported(h, g))
         return default_plan(h, g);  // the plain kernel is the only candidate
     const size_t n = (size_t)(g.n0 * g.n1 * g.n2);
     double *a = nullptr, *b = nullptr;
@@ -245,8 +273,9 @@ Plan plan_for(const stencil_handle_s* hc, const Geo& g, int64_t T, cudaStream_t 
     if (h->dim == 3) { ext[0] = g.n0; ext[1] = g.n1; ext[2] = g.n2; }
     // probe length: enough steps to amortise a pass of the deepest candidate, bounded by T
     int64_t probe = h->dim == 1 ? 128 : (h->dim == 2 ? 48 : 8);
+    if (gs_tuned) probe = h->dim == 2 ? 64 : 32;   // two sweep blocks of the wavefront
     if (probe > T) probe = T;
-    std::vector<Plan> cands = jacobi_candidates(h, g, T);
+    std::vector<Plan> cands = gs_tuned ? gs_candidates(h) : jacobi_candidates(h, g, T);
     // the plain kernel is the reference: another plan must beat it by a clear
     // margin, so that run-to-run noise of a few percent never flips the choice
     constexpr double MARGIN = 0.97;

@@ -51,7 +51,8 @@ def test_get_plan_reports_fixed_and_tuned_plans():
     assert st.plan(u, 30) == (S.STENCIL_KERNEL_DIAMOND, 6, (0, 40, 50))
     st.set_plan(S.STENCIL_KERNEL_AUTO)
     k, tb, tile = st.plan(u, 30)
-    assert k in (S.STENCIL_KERNEL_PLAIN, S.STENCIL_KERNEL_BLOCKED, S.STENCIL_KERNEL_DIAMOND) and tb >= 1
+    assert k in (S.STENCIL_KERNEL_PLAIN, S.STENCIL_KERNEL_BLOCKED, S.STENCIL_KERNEL_DIAMOND,
+                 S.STENCIL_KERNEL_STREAM) and tb >= 1
     assert st.plan(u, 30) == (k, tb, tile)          # cached: the same answer without tuning again
     gs = S.Stencil(2, 0, 1, [0.2] * 5, S.STENCIL_GAUSS_SEIDEL)
     assert gs.plan(u, 10)[0] == S.STENCIL_KERNEL_WAVEFRONT
@@ -59,3 +60,30 @@ def test_get_plan_reports_fixed_and_tuned_plans():
     assert gp.plan(u, 10)[0] in (S.STENCIL_KERNEL_WAVEFRONT, S.STENCIL_KERNEL_PLAIN)
     for x in (st, gs, gp):
         x.close()
+
+
+# the wavefront Gauss-Seidel parameter sets the tuner times (the first is the default)
+GS_2D_STAR1 = [(0, 0, 0), (3, 16, 16), (4, 16, 16), (3, 8, 16), (2, 32, 8), (3, 32, 1)]
+
+
+@pytest.mark.parametrize("dim,shape,ext,T", [(2, "star", (700, 520), 70), (2, "box", (300, 410), 40),
+                                             (3, "star", (40, 50, 60), 33)])
+def test_auto_gauss_seidel_plan_is_timed_and_matches_oracle(dim, shape, ext, T):
+    """An automatic Gauss-Seidel plan is one of the timed wavefront parameter sets, and gives the oracle's
+    result bit for bit."""
+    import torch
+    from paper_2010_04868_gb300 import stencil as S
+    w, u0 = case(dim, shape, 1, ext, seed=91)
+    st = S.Stencil(dim, 0 if shape == "star" else 1, 1, list(w), S.STENCIL_GAUSS_SEIDEL)
+    u = torch.from_numpy(u0.copy()).cuda()
+    k, tb, tile = st.plan(u, T)
+    assert k == S.STENCIL_KERNEL_WAVEFRONT
+    if dim == 2 and shape == "star":
+        assert tuple(tile) in GS_2D_STAR1
+    elif dim == 3:
+        assert tile[0] in (0, 3, 4)
+    st.run(u, T)
+    assert st.status() == 0
+    ref = oracle_run(u0, T, dim, shape, 1, w, "gs", "constant", 0.0, "fma")
+    assert bits_equal(u.cpu().numpy(), ref)
+    st.close()
