@@ -4,9 +4,13 @@
 // Temporal tiling (Section 1, the blocking methods; Section 3.4: tiles of
 // height T_b in time) advances a tile several steps while it stays on chip.
 // Here the slowest axis (rows in 2D, planes in 3D) is streamed instead of
-// tiled: a CTA owns a cross-section tile (a strip of W2 columns in 2D, W1 x W2
-// cells in 3D, each including a halo of h = T_b r on every side) and a chunk
-// of Z rows/planes of the streamed axis. It keeps, for every time level
+// tiled: a cross-section tile (a strip of W2 columns in 2D, W1 x W2 cells in
+// 3D, each including a halo of h = T_b r on every side) is streamed over the
+// rows/planes of the slowest axis. The tiles' planes, laid end to end, are
+// shared out evenly over one wave of resident CTAs: each CTA takes the same
+// number of planes, in one or two segments (a segment ends at a tile's last
+// plane), so that all CTAs of a pass finish together. For each segment a CTA
+// keeps, for every time level
 // s = 0 .. T_b - 1, a ring of planes in shared memory and advances all levels
 // in one pass along the streamed axis:
 //   iteration it: level 0 (the input) receives M planes by TMA (issued two
@@ -15,7 +19,7 @@
 //   planes straight to the output grid. One CTA barrier per iteration.
 // Level s trails level s - 1 by M + r planes, so every value a level reads was
 // produced before the last barrier. The streamed axis needs no halo beyond the
-// chunk's T_b r planes per side, so the only redundant work is the
+// segment's T_b r planes per side, so the only redundant work is the
 // cross-section halo: about W2 / (W2 - 2h) in 2D (a warp of 32 columns is the
 // unit of cost). Compared with staging a whole 2D or 3D tile per pass, each
 // input value is loaded once per pass and nothing is decoded per point: every
@@ -43,11 +47,10 @@ struct StrGeo {
     int B1, B2;      // output tile of the cross-section (W - 2h)
     int h;           // halo T_b * r per side on the cross-section axes
     int J;           // cross-section rows per thread (W1 / blockDim.y)
-    int Z;           // chunk length along the streamed axis
+    int64_t per;     // planes of the streamed axis per CTA, the tiles' planes laid end to end
     int ns1, ns2;    // tiles along cross-section axes 1 (3D only) and 2
-    int nchunk;      // chunks along the streamed axis
+    int nblk;        // CTAs: ceil(ns1 ns2 nz / per), one balanced wave by default
     int C0, C;       // ring capacities (planes) of level 0 and of levels 1 .. T_b - 1
-    int niter;       // iterations per chunk
     int use_tma;     // level-0 planes by TMA (constant boundary) or by cp.async (periodic)
 };
 
@@ -106,19 +109,19 @@ __device__ __forceinline__ int ring_mod(int a, int c)
 constexpr int STREAM_PF = 2;
 
 // Level-0 load of planes [c0 + j M, + M) into ring slots (j M) mod C0 ...: by TMA (thread 0,
-// mbarrier j mod (STREAM_PF + 1)) or by cp.async from wrapped / checked coordinates (every
-// thread, its own cells).
+// mbarrier k mod (STREAM_PF + 1), k the CTA's running count of loads) or by cp.async from
+// wrapped / checked coordinates (every thread, its own cells).
 template <int DIM, int M>
 __device__ __forceinline__ void stream_load(const CUtensorMap* tmap, const double* __restrict__ in, const Geo& g,
                                             int bc, double c, const StrGeo& sg, double* ring0, uint32_t bar_base,
-                                            int64_t c0, int j, int64_t gj0, int64_t gx0, int jb)
+                                            int64_t c0, int j, int k, int64_t gj0, int64_t gx0, int jb)
 {
     const int P = sg.W1 * sg.W2;
     const int slot = (j * M) % sg.C0;
     const int64_t z = c0 + (int64_t)j * M;
     if (sg.use_tma) {
         if (threadIdx.x == 0 && threadIdx.y == 0) {
-            const uint32_t bar = bar_base + 8u * (uint32_t)(j % (STREAM_PF + 1));
+            const uint32_t bar = bar_base + 8u * (uint32_t)(k % (STREAM_PF + 1));
             const uint32_t bytes = (uint32_t)(M * P * 8);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -182,25 +185,11 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_stream(const __grid_constant_
 #pragma unroll
     for (int s = 1; s < TB; ++s) ring[s] = sm + (int64_t)(sg.C0 + (s - 1) * sg.C) * P;
 
-    int b = blockIdx.x;
-    const int t2 = b % sg.ns2;
-    b /= sg.ns2;
-    const int t1 = b % sg.ns1;
-    const int chunk = b / sg.ns1;
     const int64_t nz = DIM == 2 ? g.n1 : g.n0;
     const int64_t n1 = DIM == 3 ? g.n1 : 1;
-    const int64_t z0 = (int64_t)chunk * sg.Z;
-    const int64_t z1 = z0 + sg.Z < nz ? z0 + sg.Z : nz;
     const int pad = sg.h & 1;  // staged columns start one early when h is odd (TMA 16-byte rule)
-    const int64_t gj0 = DIM == 3 ? (int64_t)t1 * sg.B1 - sg.h : 0;
-    const int64_t gx0 = (int64_t)t2 * sg.B2 - sg.h - pad;
     const int x = threadIdx.x;
     const int jb = threadIdx.y * sg.J;
-    const int64_t gx = gx0 + x;
-    const bool xout = gx < 0 || gx >= g.n2;
-    const int64_t c0 = z0 - TB * R;
-    const int niter = (int)((z1 - z0 - 1 + 2 * TB * R + TB * M) / M) + 1;
-    const int64_t hi0 = z1 + TB * R;
     const bool constant = bc == BC_CONSTANT;
     const uint32_t bar_base = s_u32(&bars[0]);
     if (sg.use_tma && threadIdx.x == 0 && threadIdx.y == 0) {
@@ -208,127 +197,157 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_stream(const __grid_constant_
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_base + 8u * i) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // cells outside the grid hold c in every plane of the rings of levels 1 .. TB - 1
-    if (constant && TB > 1) {
-        for (int jj = jb; jj < jb + sg.J; ++jj) {
-            const int64_t gj = gj0 + jj;
-            if (xout || (DIM == 3 && (gj < 0 || gj >= n1)))
-                for (int s = 1; s < TB; ++s)
-                    for (int sl = 0; sl < sg.C; ++sl) ring[s][(int64_t)sl * P + jj * sg.W2 + x] = c;
-        }
-    }
-    __syncthreads();
     griddep_wait();  // launched programmatically: the previous pass has finished writing its output
 
-    // the first STREAM_PF loads (one cp.async group each, possibly empty)
-    for (int j = 0; j < STREAM_PF; ++j) {
-        if (j < niter && c0 + (int64_t)j * M < hi0)
-            stream_load<DIM, M>(&tmap, in, g, bc, c, sg, ring[0], bar_base, c0, j, gj0, gx0, jb);
-        if (!sg.use_tma) asm volatile("cp.async.commit_group;" ::: "memory");
-    }
-
-    for (int it = 0; it < niter; ++it) {
-        // (a) the load of level-0 planes for iteration it + STREAM_PF; its slots were last read
-        //     before the previous barrier
-        if (it + STREAM_PF < niter && c0 + (int64_t)(it + STREAM_PF) * M < hi0)
-            stream_load<DIM, M>(&tmap, in, g, bc, c, sg, ring[0], bar_base, c0, it + STREAM_PF, gj0, gx0, jb);
-        // (b) the planes loaded for iteration it are complete (and set to c where outside the grid);
-        //     they are first read in iteration it + 1, after the barrier below
-        if (!sg.use_tma) {
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            asm volatile("cp.async.wait_group %0;" ::"n"(STREAM_PF) : "memory");
-        } else if (c0 + (int64_t)it * M < hi0) {
-            const uint32_t bar = bar_base + 8u * (uint32_t)(it % (STREAM_PF + 1));
-            const uint32_t par = (uint32_t)((it / (STREAM_PF + 1)) & 1);
-            if (!mbar_wait_parity(bar, par)) {
-                if (x == 0 && threadIdx.y == 0) atomicExch(status, DEV_TIMEOUT);
-                mbar_wait_parity_backoff(bar, par);
-            }
-            if (constant && c != 0.0) {
-                const int slot = (it * M) % sg.C0;
-                for (int m = 0; m < M; ++m) {
-                    const int64_t zz = c0 + (int64_t)it * M + m;
-                    const bool zout = zz < 0 || zz >= nz;
-                    for (int jj = jb; jj < jb + sg.J; ++jj) {
-                        const int64_t gj = gj0 + jj;
-                        if (zout || xout || (DIM == 3 && (gj < 0 || gj >= n1)))
-                            ring[0][(int64_t)(slot + m) * P + jj * sg.W2 + x] = c;
-                    }
-                }
-            }
-        }
-        // (c) every level advances M planes, from planes finished before the last barrier
-#pragma unroll
-        for (int s = 1; s <= TB; ++s) {
-            const int64_t cs = c0 - (int64_t)s * (M + R);
-            const int64_t y0 = cs + (int64_t)it * M;
-            const int64_t lo = z0 - (int64_t)(TB - s) * R, hi = z1 + (int64_t)(TB - s) * R;
-            if (y0 + M <= lo || y0 >= hi) continue;
-            const int lo_col = pad + s * R, hi_col = pad + 2 * sg.h + sg.B2 - s * R;
-            if (x < lo_col || x >= hi_col) continue;
-            const double* src = ring[s - 1];
-            const int Cin = s == 1 ? sg.C0 : sg.C;
-            const int64_t cin = c0 - (int64_t)(s - 1) * (M + R);
-            int so[M + 2 * R];  // plane offsets of the input rows y0 - R .. y0 + M - 1 + R
-            {
-                const int s0 = ring_mod((int)(y0 - R - cin), Cin);
-#pragma unroll
-                for (int i = 0; i < M + 2 * R; ++i) {
-                    int t = s0 + i;
-                    if (t >= Cin) t -= Cin;
-                    so[i] = t * P;
-                }
-            }
-            int oo[M];  // plane offsets of the output rows in this level's ring
-            {
-                const int d0 = (it * M) % sg.C;
-#pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    int t = d0 + m;
-                    if (t >= sg.C) t -= sg.C;
-                    oo[m] = t * P;
-                }
-            }
+    // This CTA's planes: [a, e) of the tiles' planes laid end to end (tile-major), split into
+    // segments at tile boundaries; every CTA gets the same number of planes.
+    const int64_t total = (int64_t)sg.ns1 * sg.ns2 * nz;
+    int64_t a = (int64_t)blockIdx.x * sg.per;
+    const int64_t e = a + sg.per < total ? a + sg.per : total;
+    int kbase = 0;  // level-0 loads issued by earlier segments (mbarrier phases)
+    while (a < e) {
+        const int64_t tile = a / nz;
+        const int64_t z0 = a - tile * nz;
+        const int64_t z1 = z0 + (e - a) < nz ? z0 + (e - a) : nz;
+        const int t2 = (int)(tile % sg.ns2);
+        const int t1 = (int)(tile / sg.ns2);
+        const int64_t gj0 = DIM == 3 ? (int64_t)t1 * sg.B1 - sg.h : 0;
+        const int64_t gx0 = (int64_t)t2 * sg.B2 - sg.h - pad;
+        const int64_t gx = gx0 + x;
+        const bool xout = gx < 0 || gx >= g.n2;
+        const int64_t c0 = z0 - TB * R;
+        const int niter = (int)((z1 - z0 - 1 + 2 * TB * R + TB * M) / M) + 1;
+        const int64_t hi0 = z1 + TB * R;
+        // cells outside the grid hold c in every plane of the rings of levels 1 .. TB - 1
+        if (constant && TB > 1) {
             for (int jj = jb; jj < jb + sg.J; ++jj) {
-                if (DIM == 3 && (jj < s * R || jj >= sg.W1 - s * R)) continue;
                 const int64_t gj = gj0 + jj;
-                if (constant && (xout || (DIM == 3 && (gj < 0 || gj >= n1)))) continue;  // keeps c
-                const int cell = jj * sg.W2 + x;
-                double acc[M];
-#pragma unroll
-                for (int q = 0; q < K; ++q) {
-                    const int dz = S::o(q, ZA), dj = DIM == 3 ? S::o(q, 1) : 0, dx = S::o(q, 2);
-                    const int co = cell + dj * sg.W2 + dx;
-#pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        const double v = src[so[m + R + dz] + co];
-                        acc[m] = q == 0 ? __dmul_rn(w.w[0], v) : acc_step<ARITH>(acc[m], w.w[q], v);
-                    }
+                if (xout || (DIM == 3 && (gj < 0 || gj >= n1)))
+                    for (int s = 1; s < TB; ++s)
+                        for (int sl = 0; sl < sg.C; ++sl) ring[s][(int64_t)sl * P + jj * sg.W2 + x] = c;
+            }
+        }
+        __syncthreads();  // the rings are free (the previous segment is done) and the barriers initialised
+
+        // the first STREAM_PF loads (one cp.async group each, possibly empty)
+        for (int j = 0; j < STREAM_PF; ++j) {
+            if (j < niter && c0 + (int64_t)j * M < hi0)
+                stream_load<DIM, M>(&tmap, in, g, bc, c, sg, ring[0], bar_base, c0, j, kbase + j, gj0, gx0, jb);
+            if (!sg.use_tma) asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+
+        for (int it = 0; it < niter; ++it) {
+            // (a) the load of level-0 planes for iteration it + STREAM_PF; its slots were last read
+            //     before the previous barrier
+            if (it + STREAM_PF < niter && c0 + (int64_t)(it + STREAM_PF) * M < hi0)
+                stream_load<DIM, M>(&tmap, in, g, bc, c, sg, ring[0], bar_base, c0, it + STREAM_PF,
+                                    kbase + it + STREAM_PF, gj0, gx0, jb);
+            // (b) the planes loaded for iteration it are complete (and set to c where outside the grid);
+            //     they are first read in iteration it + 1, after the barrier below
+            if (!sg.use_tma) {
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                asm volatile("cp.async.wait_group %0;" ::"n"(STREAM_PF) : "memory");
+            } else if (c0 + (int64_t)it * M < hi0) {
+                const int k = kbase + it;
+                const uint32_t bar = bar_base + 8u * (uint32_t)(k % (STREAM_PF + 1));
+                const uint32_t par = (uint32_t)((k / (STREAM_PF + 1)) & 1);
+                if (!mbar_wait_parity(bar, par)) {
+                    if (x == 0 && threadIdx.y == 0) atomicExch(status, DEV_TIMEOUT);
+                    mbar_wait_parity_backoff(bar, par);
                 }
-                if (s < TB) {
-                    double* dst = ring[s < TB ? s : 0];
-#pragma unroll
+                if (constant && c != 0.0) {
+                    const int slot = (it * M) % sg.C0;
                     for (int m = 0; m < M; ++m) {
-                        const int64_t y = y0 + m;
-                        if (y < lo || y >= hi) continue;
-                        dst[oo[m] + cell] = (constant && (y < 0 || y >= nz)) ? c : acc[m];
-                    }
-                } else {
-                    // the last level: the output tile, inside the grid
-                    const int lx = x - pad - sg.h;
-                    const int lj = DIM == 3 ? jj - sg.h : 0;
-                    if (lx < 0 || lx >= sg.B2 || gx >= g.n2) continue;
-                    if (DIM == 3 && (lj < 0 || lj >= sg.B1 || gj >= n1)) continue;
-#pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        const int64_t y = y0 + m;
-                        if (y < lo || y >= hi) continue;
-                        out[(DIM == 3 ? y * n1 + gj : y) * g.n2 + gx] = acc[m];
+                        const int64_t zz = c0 + (int64_t)it * M + m;
+                        const bool zout = zz < 0 || zz >= nz;
+                        for (int jj = jb; jj < jb + sg.J; ++jj) {
+                            const int64_t gj = gj0 + jj;
+                            if (zout || xout || (DIM == 3 && (gj < 0 || gj >= n1)))
+                                ring[0][(int64_t)(slot + m) * P + jj * sg.W2 + x] = c;
+                        }
                     }
                 }
             }
+            // (c) every level advances M planes, from planes finished before the last barrier
+    #pragma unroll
+            for (int s = 1; s <= TB; ++s) {
+                const int64_t cs = c0 - (int64_t)s * (M + R);
+                const int64_t y0 = cs + (int64_t)it * M;
+                const int64_t lo = z0 - (int64_t)(TB - s) * R, hi = z1 + (int64_t)(TB - s) * R;
+                if (y0 + M <= lo || y0 >= hi) continue;
+                const int lo_col = pad + s * R, hi_col = pad + 2 * sg.h + sg.B2 - s * R;
+                if (x < lo_col || x >= hi_col) continue;
+                const double* src = ring[s - 1];
+                const int Cin = s == 1 ? sg.C0 : sg.C;
+                const int64_t cin = c0 - (int64_t)(s - 1) * (M + R);
+                int so[M + 2 * R];  // plane offsets of the input rows y0 - R .. y0 + M - 1 + R
+                {
+                    const int s0 = ring_mod((int)(y0 - R - cin), Cin);
+    #pragma unroll
+                    for (int i = 0; i < M + 2 * R; ++i) {
+                        int t = s0 + i;
+                        if (t >= Cin) t -= Cin;
+                        so[i] = t * P;
+                    }
+                }
+                int oo[M];  // plane offsets of the output rows in this level's ring
+                {
+                    const int d0 = (it * M) % sg.C;
+    #pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        int t = d0 + m;
+                        if (t >= sg.C) t -= sg.C;
+                        oo[m] = t * P;
+                    }
+                }
+                for (int jj = jb; jj < jb + sg.J; ++jj) {
+                    if (DIM == 3 && (jj < s * R || jj >= sg.W1 - s * R)) continue;
+                    const int64_t gj = gj0 + jj;
+                    if (constant && (xout || (DIM == 3 && (gj < 0 || gj >= n1)))) continue;  // keeps c
+                    const int cell = jj * sg.W2 + x;
+                    double acc[M];
+    #pragma unroll
+                    for (int q = 0; q < K; ++q) {
+                        const int dz = S::o(q, ZA), dj = DIM == 3 ? S::o(q, 1) : 0, dx = S::o(q, 2);
+                        const int co = cell + dj * sg.W2 + dx;
+    #pragma unroll
+                        for (int m = 0; m < M; ++m) {
+                            const double v = src[so[m + R + dz] + co];
+                            acc[m] = q == 0 ? __dmul_rn(w.w[0], v) : acc_step<ARITH>(acc[m], w.w[q], v);
+                        }
+                    }
+                    if (s < TB) {
+                        double* dst = ring[s < TB ? s : 0];
+    #pragma unroll
+                        for (int m = 0; m < M; ++m) {
+                            const int64_t y = y0 + m;
+                            if (y < lo || y >= hi) continue;
+                            dst[oo[m] + cell] = (constant && (y < 0 || y >= nz)) ? c : acc[m];
+                        }
+                    } else {
+                        // the last level: the output tile, inside the grid
+                        const int lx = x - pad - sg.h;
+                        const int lj = DIM == 3 ? jj - sg.h : 0;
+                        if (lx < 0 || lx >= sg.B2 || gx >= g.n2) continue;
+                        if (DIM == 3 && (lj < 0 || lj >= sg.B1 || gj >= n1)) continue;
+    #pragma unroll
+                        for (int m = 0; m < M; ++m) {
+                            const int64_t y = y0 + m;
+                            if (y < lo || y >= hi) continue;
+                            out[(DIM == 3 ? y * n1 + gj : y) * g.n2 + gx] = acc[m];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        // loads issued in this segment: j = 0 .. while c0 + j M < hi0, below niter
+        {
+            const int64_t need = (hi0 - c0 + M - 1) / M;
+            kbase += (int)(need < niter ? need : niter);
+        }
+        if (!sg.use_tma) asm volatile("cp.async.wait_all;" ::: "memory");
+        a += z1 - z0;
     }
 }
 
@@ -417,25 +436,32 @@ static size_t make_str(const stencil_handle_s* h, const Geo& g, int tb, const in
     sg.C = 2 * M + 2 * r;
     sg.ns2 = (int)((g.n2 + sg.B2 - 1) / sg.B2);
     sg.ns1 = dim == 3 ? (int)((n1 + sg.B1 - 1) / sg.B1) : 1;
-    int64_t Z = tile && tile[0] > 0 ? tile[0] : 0;
-    if (Z <= 0) {
-        // about 8 CTAs per SM, so that the last wave of every pass is a small part of it
-        int nsm = 152, dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const int64_t tiles = (int64_t)sg.ns1 * sg.ns2;
-        const int64_t want = (8 * (int64_t)nsm + tiles - 1) / tiles;
-        Z = (nz + want - 1) / want;
-        if (Z < 2 * M) Z = 2 * M;
-    }
-    if (Z > nz) Z = nz;
-    sg.Z = (int)Z;
-    sg.nchunk = (int)((nz + Z - 1) / Z);
-    sg.niter = (int)((Z - 1 + 2 * tb * r + tb * M) / M) + 1;
+    sg.per = tile && tile[0] > 0 ? tile[0] : 0;  // 0: set from the occupancy (stream_balance)
+    sg.nblk = 0;
     const int64_t planes = sg.C0 + (int64_t)(tb - 1) * sg.C;
     const size_t smem = (size_t)planes * sg.W1 * sg.W2 * sizeof(double);
-    if (smem > 227 * 1024 || (int64_t)sg.ns1 * sg.ns2 * sg.nchunk > 0x7fffffffLL) return 0;
+    if (smem > 227 * 1024) return 0;
     return smem;
+}
+
+// Planes per CTA: by default the tiles' planes shared out evenly over one wave of resident CTAs
+// (occ per SM), so that every CTA of a pass finishes at about the same time; at least 2 M.
+static bool stream_balance(StrGeo& sg, const Geo& g, int dim, int occ, int M)
+{
+    int nsm = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t nz = dim == 2 ? g.n1 : g.n0;
+    const int64_t total = (int64_t)sg.ns1 * sg.ns2 * nz;
+    if (sg.per <= 0) {
+        const int64_t slots = (int64_t)nsm * (occ > 0 ? occ : 1);
+        sg.per = (total + slots - 1) / slots;
+    }
+    if (sg.per < 2 * M) sg.per = 2 * M;
+    const int64_t nblk = (total + sg.per - 1) / sg.per;
+    if (nblk > 0x7fffffffLL) return false;
+    sg.nblk = (int)nblk;
+    return true;
 }
 
 static bool stream_map(CUtensorMap& m, const double* base, const Geo& g, int dim, const StrGeo& sg, int M)
@@ -488,7 +514,13 @@ static int stream_passes(const RunCtx& ctx, double*& src, double*& dst, int64_t 
     bool tma = ctx.h->bc == BC_CONSTANT && stream_map(mapA, src, ctx.g, DIM, sg, M) &&
                stream_map(mapB, dst, ctx.g, DIM, sg, M);
     sg.use_tma = tma ? 1 : 0;
-    const unsigned nblk = (unsigned)((int64_t)sg.ns1 * sg.ns2 * sg.nchunk);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (int)(block.x * block.y), smem) != cudaSuccess) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    if (!stream_balance(sg, ctx.g, DIM, occ, M)) return STENCIL_EUNSUPPORTED;
+    const unsigned nblk = (unsigned)sg.nblk;
     const double* a0 = src;
     for (int64_t p = 0; p < npass; ++p) {
         const CUtensorMap& map = src == a0 ? mapA : mapB;
