@@ -116,7 +116,13 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
  *            with radius 1, tile[2] = points per lane and step of the
  *            one-warp tile (8 or 16), or 1 for the decoupled tile of the
  *            5-point star with one weight per term (a chain warp, producer
- *            warps and a scheduler warp per tile); 0 = default.
+ *            warps and a scheduler warp per tile); for WAVEFRONT with a
+ *            periodic boundary (the in-sweep tile DAG), tile[0] and tile[1] =
+ *            lines per tile along axes 0 (3D) and 1, one thread each, at most
+ *            256 in all, and tile[2] = hyperplane steps per tile; for STREAM,
+ *            tile[0] = planes of the slowest axis per CTA (0: shared out
+ *            evenly over one wave of resident CTAs), tile[1] = staged rows
+ *            (3D), tile[2] = staged columns; 0 = default.
  * A family that cannot run a given (method, boundary, grid) makes stencil_run
  * return EUNSUPPORTED.
  *

@@ -1163,12 +1163,18 @@ static int sweep_dag(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
     t.cp1 = box ? 1 + R : 1;
     t.cp0 = DIM == 3 ? (box ? 1 + R * (t.cp1 + 1) : 1) : 0;
     t.skew = (DIM == 3 && box) ? R : 0;
-    // small tiles: a sweep's critical path is about nt0 + nt1 + nts tiles long
+    // small tiles: a sweep's critical path is about nt0 + nt1 + nts tiles long. The plan may set
+    // the lines per tile along axes 0 and 1 (tile[0], tile[1]; one thread each, at most 256 in
+    // all) and the hyperplane steps per tile (tile[2]).
     if (DIM == 3) {
         t.b0 = 8; t.b1 = 8; t.bs = 16;
     } else {
         t.b0 = 1; t.b1 = 64; t.bs = 32;
     }
+    if (DIM == 3 && ctx.wtile[0] > 0) t.b0 = (int)std::min<int64_t>(ctx.wtile[0], 256);
+    if (ctx.wtile[1] > 0) t.b1 = (int)std::min<int64_t>(ctx.wtile[1], 256);
+    if (ctx.wtile[2] > 0) t.bs = (int)std::min<int64_t>(ctx.wtile[2], 1024);
+    if (t.b0 * t.b1 > 256) t.b1 = 256 / t.b0;
     const int64_t thmax = t.cp0 * (g.n0 - 1) + t.cp1 * (g.n1 - 1) + (g.n2 - 1);
     t.nt0 = (g.n0 + t.b0 - 1) / t.b0;
     t.nt1 = (g.n1 + t.skew * (g.n0 - 1) + t.b1 - 1) / t.b1;

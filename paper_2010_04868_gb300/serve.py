@@ -436,7 +436,9 @@ def main():
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--cap", type=float, default=40e9, help="device-memory arena in bytes")
     ap.add_argument("--rates", default="0.5,0.8,1.1", help="arrival rates as multiples of the measured capacity")
-    ap.add_argument("--plain-per-class", type=int, default=8,
+    ap.add_argument("--capacity-requests", type=int, default=2000,
+                    help="requests of the mix (a prefix) served all at once to measure the capacity")
+    ap.add_argument("--plain-per-class", type=int, default=6,
                     help="requests per operator class whose plain one-at-a-time service time is measured at full T")
     args = ap.parse_args()
     import torch
@@ -449,13 +451,12 @@ def main():
     prepare(ex, reqs)
     torch.cuda.synchronize()
     prep_s = time.perf_counter() - t0
-    # capacity of this server: everything arrives at once
-    for r in reqs:
-        r.arrival = 0.0
-    sat = Server(ex, args.slots, cap).serve(reqs).summary()
+    # capacity of this server: a prefix of the mix, everything arriving at once
+    head = [Request(r.rid, r.method, r.dim, r.shape, r.ext, r.T, r.seed) for r in reqs[:args.capacity_requests]]
+    sat = Server(ex, args.slots, cap).serve(head).summary()
     capacity = sat["req_per_s"]
     out = {"requests": args.requests, "slots": args.slots, "arena_gb": cap / 1e9, "prepare_s": round(prep_s, 1),
-           "saturated": sat, "rates": []}
+           "saturated": dict(sat, requests=len(head)), "rates": []}
     for m in [float(x) for x in args.rates.split(",")]:
         rate = m * capacity
         poisson_arrivals(reqs, rate)

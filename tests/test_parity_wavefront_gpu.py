@@ -153,3 +153,14 @@ def test_gs2d_decoupled_tile_equals_one_warp_tile(ext):
         a = gpu_run(u0, 70, 2, "star", 1, w, "gs", "constant", 0.2, arith, plan=WAVE, tile=(0, 0, 1))
         b = gpu_run(u0, 70, 2, "star", 1, w, "gs", "constant", 0.2, arith, plan=WAVE)
         assert bits_equal(a, b), (arith, first_diff(a, b))
+
+
+@pytest.mark.parametrize("dim,r,ext,tile", [(3, 1, (13, 11, 17), (4, 8, 16)), (3, 1, (20, 9, 12), (1, 32, 8)),
+                                            (3, 2, (11, 12, 13), (2, 16, 5)), (2, 1, (70, 45), (0, 32, 32)),
+                                            (2, 2, (33, 40), (0, 32, 7))])
+def test_periodic_sweep_dag_tile_shapes(dim, r, ext, tile):
+    """The in-sweep DAG with the tile shape a plan fixes (lines per tile along axes 0 and 1, hyperplane steps)."""
+    w, u0 = case(dim, "star", r, ext, seed=dim * 31 + r)
+    ref = oracle_run(u0, 5, dim, "star", r, w, "gs", "periodic", 0.0, "fma")
+    got = gpu_run(u0, 5, dim, "star", r, w, "gs", "periodic", 0.0, "fma", plan=WAVE, tile=tile)
+    assert bits_equal(got, ref), first_diff(got, ref)
