@@ -11,6 +11,7 @@
 //   * warps per SM (CTAs per SM x warps per CTA: latency hiding across warps),
 //   * the instruction (DFMA, DADD, DMUL, and the three interleaved),
 //   * the operands (two shared scalars, or a distinct register triple per chain),
+//   * stencil-shaped streams: 5-term weighted sums, weights from the constant bank or registers,
 // and the best rate is the FP64 peak reported. Also: the dependent-chain latency of one
 // DFMA and the cost of a warp instruction with one active lane.
 //
@@ -71,6 +72,53 @@ __global__ void stream_ops(double* out, long long* rec, int iters, double a, dou
     double s = 0;
 #pragma unroll
     for (int c = 0; c < CH; ++c) s += x[c];
+    if (s == 12345.678) out[0] = s;
+    __syncthreads();
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) {
+        rec[3 * blockIdx.x] = smid();
+        rec[3 * blockIdx.x + 1] = t0;
+        rec[3 * blockIdx.x + 2] = t1;
+    }
+}
+
+// A stencil-shaped stream: per chain a 5-term weighted sum (one DMUL, four dependent DFMAs) whose
+// result feeds the chain's next sum, weights read from the constant bank (REGW = 0) or forced into
+// registers with an empty asm (REGW = 1), the values in registers.
+__constant__ double c_w5[5] = {0.2, 0.21, 0.18, 0.22, 0.19};
+
+template <int CH, int REGW>
+__global__ void stream_stencil(double* out, long long* rec, int iters, double a, double b, int active)
+{
+    const long long t0 = clock64();
+    double wq[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        wq[q] = c_w5[q];
+        if (REGW) asm volatile("" : "+d"(wq[q]));
+    }
+    double v[CH][5];
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            v[c][q] = threadIdx.x * 1e-9 + c * 0.1 + q * a + b;
+            asm volatile("" : "+d"(v[c][q]));
+        }
+    if ((int)(threadIdx.x & 31) < active) {
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                double acc = __dmul_rn(wq[0], v[c][0]);
+#pragma unroll
+                for (int q = 1; q < 5; ++q) acc = __fma_rn(wq[q], v[c][q], acc);
+                v[c][0] = acc;
+            }
+        }
+    }
+    double s = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) s += v[c][0];
     if (s == 12345.678) out[0] = s;
     __syncthreads();
     const long long t1 = clock64();
@@ -184,6 +232,11 @@ static void add_shapes(std::vector<Shape>& v, bool full)
             v.push_back(Shape{"mix", stream_ops<CH, 3>, CH, threads, ctas, 32});
         }
         v.push_back(Shape{"dfma_reg3", stream_ops<CH, 4>, CH, threads, ctas, 32});
+        if (full && CH <= 4) {
+            // 5 FP64 instructions per chain and iteration: counted as 5 "chains" of one
+            v.push_back(Shape{"stencil5_const", stream_stencil<CH, 0>, 5 * CH, threads, ctas, 32});
+            v.push_back(Shape{"stencil5_reg", stream_stencil<CH, 1>, 5 * CH, threads, ctas, 32});
+        }
     }
 }
 

@@ -349,13 +349,25 @@ def tune_keys(reqs):
     return list(seen.values())
 
 
-def prepare(ex: GpuExecutor, reqs):
+def prepare(ex: GpuExecutor, reqs, grow: bool = True):
     """Outside any measurement: tune every plan the requests will use, and run one request of each
-    class in every slot (first launches, workspaces grown to the class's largest request)."""
+    class in every slot (first launches; with grow, workspaces grown to the class's largest
+    request, else a small request of each class)."""
     torch = ex.torch
     for r in tune_keys(reqs):
         u, _ = ex.views(r, 0)
         ex.handles[0][r.cls].plan(u, r.T)
+    if not grow:
+        small = {}
+        for r in reqs:
+            if r.cls not in small or r.updates < small[r.cls].updates:
+                small[r.cls] = r
+        for slot in range(len(ex.streams)):
+            for r in small.values():
+                job = ex.start(Request(-1, r.method, r.dim, r.shape, r.ext, 2, r.seed), 0, slot)
+                torch.cuda.synchronize()
+                ex.finish(job)
+        return
     largest = {}
     for r in reqs:
         if r.cls not in largest or r.points > largest[r.cls].points:
@@ -372,7 +384,7 @@ def prepare(ex: GpuExecutor, reqs):
 def service_times(reqs, plan=None, mem_cap: int = 8 * 10 ** 9):
     """Seconds each request takes alone on a one-slot server (input generation and the full T solve)."""
     ex = GpuExecutor(1, mem_cap, plan=plan)
-    prepare(ex, reqs)
+    prepare(ex, reqs, grow=False)
     out = []
     for r in reqs:
         t0 = time.perf_counter()
