@@ -805,7 +805,10 @@ __global__ void k_wave_prefix(WaveGeo wg, int64_t* pre)
 // persistent launch runs all T sweeps: tiles are handed out in (sweep,
 // diagonal) order, each waits (bounded) for its three lower neighbours of the
 // same sweep and for every tile of the previous sweep, computes its points in
-// theta order (one CTA barrier per theta), and publishes its flag.
+// theta order (one CTA barrier per theta), and publishes its flag. A tile of sweep s waits only for
+// the tiles of sweep s - 1 it depends on (sweep_dag_prev_waits), so about three sweeps can be in
+// flight at once: the wrap makes a sweep's first points depend on the previous sweep's last
+// hyperplanes of each axis, a lag of about one extent per axis, not a whole sweep.
 
 struct SweepDag {
     int b0, b1, bs, cp0, cp1, skew;   // tile extents in (i, sigma, theta), hyperplane weights, sigma skew
@@ -832,6 +835,46 @@ __global__ void k_sweepdag_prefix(SweepDag t, int64_t* pre)
         pre[0] = 0;
         for (int64_t d = 0; d < t.Dn; ++d) pre[d + 1] += pre[d];
     }
+}
+
+// Tiles of the previous sweep a tile (T0, T1, TS) must wait for (flag indices; returns how many).
+// A tile's completion implies that of every tile of its sweep with no larger coordinates, so one
+// "highest" tile stands for a set:
+//   (a) the tile beyond this one by the radius in every coordinate: every point within the radius of
+//       this tile's points, whose old values it reads and which read, in the previous sweep, the
+//       values this tile overwrites;
+//   (b) for points within r of the low face of an axis, the tiles holding the wrapped neighbours at
+//       the high end of that axis: they must hold the previous sweep's values when read, and they
+//       read this tile's points (their wrapped + neighbours) in the previous sweep before these are
+//       overwritten.
+// Everything else a point reads is of its own sweep and is ordered by the in-sweep waits.
+template <int DIM, int R>
+__device__ __forceinline__ int sweep_dag_prev_waits(const SweepDag& t, const Geo& g, int64_t T0, int64_t T1,
+                                                    int64_t TS, int64_t* out)
+{
+    auto cdiv = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
+    auto idx = [&](int64_t a, int64_t b, int64_t c) {
+        a = a < t.nt0 - 1 ? a : t.nt0 - 1;
+        b = b < t.nt1 - 1 ? b : t.nt1 - 1;
+        c = c < t.nts - 1 ? c : t.nts - 1;
+        return (a * t.nt1 + b) * t.nts + c;
+    };
+    int n = 0;
+    out[n++] = idx(T0 + cdiv(R, t.b0), T1 + cdiv(R, t.b1), TS + cdiv(R, t.bs));
+    // extents of the tile's points (the star has no sigma skew)
+    const int64_t i_lo = T0 * t.b0, i_hi = (T0 + 1) * t.b0 - 1 < g.n0 - 1 ? (T0 + 1) * t.b0 - 1 : g.n0 - 1;
+    const int64_t j_lo = T1 * t.b1, j_hi = (T1 + 1) * t.b1 - 1 < g.n1 - 1 ? (T1 + 1) * t.b1 - 1 : g.n1 - 1;
+    const int64_t th_lo = TS * t.bs, th_hi = th_lo + t.bs - 1;
+    // the fast axis: points with k < R exist where theta - cp0 i - cp1 j < R
+    if (th_lo < (int64_t)t.cp0 * i_hi + (int64_t)t.cp1 * j_hi + R)
+        out[n++] = idx(T0, T1, ((int64_t)t.cp0 * i_hi + (int64_t)t.cp1 * j_hi + (g.n2 - 1)) / t.bs);
+    // axis 1: rows j < R; their wrapped neighbours sit in the last row tile, theta up to
+    // cp0 i + cp1 (n1 - 1) + k with k <= theta - cp0 i
+    if (j_lo < R)
+        out[n++] = idx(T0, t.nt1 - 1, ((int64_t)t.cp1 * (g.n1 - 1) + th_hi) / t.bs);
+    // axis 0 (3D): planes i < R; wrapped neighbours in the last plane tile, theta up to cp0 (n0 - 1) + theta
+    if (DIM == 3 && i_lo < R) out[n++] = idx(t.nt0 - 1, T1, ((int64_t)t.cp0 * (g.n0 - 1) + th_hi) / t.bs);
+    return n;
 }
 
 template <int DIM, int SHAPE, int R, int ARITH, class WS>
@@ -875,16 +918,16 @@ __global__ void __launch_bounds__(256) k_gs_sweepdag(double* __restrict__ u, Geo
                 s_T1 = T1;
                 s_TS = TS;
                 s_sw = sw;
-                // the whole previous sweep, then the three lower neighbours of this sweep
+                // the three lower neighbours of this sweep, then what this tile needs of the previous
+                // sweep (sweep_dag_prev_waits)
                 bool ok = true;
-                int it = 0;
-                while (ld_acquire64(finished) < (unsigned long long)(sw * t.sweep_units) && it < wc.spin) {
-                    __nanosleep(it < 64 ? 32 : 256);
-                    ++it;
-                }
-                ok &= it < wc.spin;
                 const int tag = (int)sw + 1;
                 const int64_t f = (T0 * t.nt1 + T1) * t.nts + TS;
+                if (sw > 0) {
+                    int64_t pw[4];
+                    const int np = sweep_dag_prev_waits<DIM, R>(t, g, T0, T1, TS, pw);
+                    for (int q = 0; q < np; ++q) ok &= wait_flag_ge(flags + pw[q], (int)sw, wc.spin);
+                }
                 if (T0 > 0) ok &= wait_flag_ge(flags + f - t.nt1 * t.nts, tag, wc.spin);
                 if (T1 > 0) ok &= wait_flag_ge(flags + f - t.nts, tag, wc.spin);
                 if (TS > 0) ok &= wait_flag_ge(flags + f - 1, tag, wc.spin);
