@@ -128,7 +128,7 @@ def test_random_orders_that_respect_the_waits_give_the_oracle_result(dim, ext, r
     T = 3
     t, inst, reads, writes, waits = build(dim, ext, r, tiles, T)
     w, u0 = case(dim, "star", r, ext, seed=dim * 7 + r)
-    canonical = sorted(star_offsets(dim, r) + [(0, 0, 0)])                           # lexicographic, slowest axis first
+    canonical = sorted(star_offsets(dim, r) + [(0, 0, 0)])   # lexicographic, slowest axis first
     terms = list(reversed(list(zip(canonical, w))))    # descending canonical order
     ref = oracle_run(u0, T, dim, "star", r, w, "gs", "periodic", 0.0, "unfused")
     n = (t["n0"], t["n1"], t["n2"])
