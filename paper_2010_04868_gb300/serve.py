@@ -451,7 +451,10 @@ def main():
     ap.add_argument("--capacity-requests", type=int, default=2000,
                     help="requests of the mix (a prefix) served all at once to measure the capacity")
     ap.add_argument("--plain-per-class", type=int, default=6,
-                    help="requests per operator class whose plain one-at-a-time service time is measured at full T")
+                    help="requests per operator class whose plain one-at-a-time service time is measured at full T "
+                         "(0: not measured)")
+    ap.add_argument("--capacity", type=float, default=0.0,
+                    help="use this capacity (requests/s, from an earlier run) instead of measuring it")
     args = ap.parse_args()
     import torch
 
@@ -464,17 +467,25 @@ def main():
     torch.cuda.synchronize()
     prep_s = time.perf_counter() - t0
     # capacity of this server: a prefix of the mix, everything arriving at once
-    head = [Request(r.rid, r.method, r.dim, r.shape, r.ext, r.T, r.seed) for r in reqs[:args.capacity_requests]]
-    sat = Server(ex, args.slots, cap).serve(head).summary()
-    capacity = sat["req_per_s"]
     out = {"requests": args.requests, "slots": args.slots, "arena_gb": cap / 1e9, "prepare_s": round(prep_s, 1),
-           "saturated": dict(sat, requests=len(head)), "rates": []}
+           "rates": []}
+    if args.capacity > 0:
+        capacity = args.capacity
+        out["capacity_given_req_s"] = capacity
+    else:
+        head = [Request(r.rid, r.method, r.dim, r.shape, r.ext, r.T, r.seed) for r in reqs[:args.capacity_requests]]
+        sat = Server(ex, args.slots, cap).serve(head).summary()
+        capacity = sat["req_per_s"]
+        out["saturated"] = dict(sat, requests=len(head))
     for m in [float(x) for x in args.rates.split(",")]:
         rate = m * capacity
         poisson_arrivals(reqs, rate)
         st = Server(ex, args.slots, cap).serve(reqs).summary()
         out["rates"].append({"multiple_of_capacity": m, "rate_req_s": round(rate, 3), "ours": st})
     ex.close()
+    if args.plain_per_class <= 0:
+        print(json.dumps(out))
+        return
     # the plain kernels, one request at a time: service times measured at full T on a stratified sample,
     # a per-class linear model (seconds = a + b * updates) for the rest, FIFO at the same arrival times
     sample = stratified_sample(reqs, args.plain_per_class)
