@@ -143,8 +143,9 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the method_configs sections")
-    ap.add_argument("--serve-requests", type=int, default=240)
-    ap.add_argument("--serve-rate", type=float, default=12.0, help="arrival rate (requests/s) of the serving section")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-rate", type=float, default=20.0, help="arrival rate (requests/s) of the serving section")
+    ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--source-hash", action="store_true")
     return ap.parse_args()
 
@@ -650,7 +651,7 @@ def _batch512(roofs, dev, reps):
 def _serving(args, dev):
     from paper_2010_04868_gb300 import serve
     sampler = ClockSampler(dev.index or 0).start()
-    out = serve.bench_run(args.serve_requests, args.serve_rate)
+    out = serve.bench_run(args.serve_requests, args.serve_rate, slots=args.serve_slots)
     out["clocks"] = sampler.stop()
     return out
 
