@@ -122,7 +122,9 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
  *            256 in all, and tile[2] = hyperplane steps per tile; for STREAM,
  *            tile[0] = planes of the slowest axis per CTA (0: shared out
  *            evenly over one wave of resident CTAs), tile[1] = staged rows
- *            (3D), tile[2] = staged columns; 0 = default.
+ *            (3D), tile[2] = staged columns; for PLAIN Jacobi in 2D/3D with
+ *            radius 1 and one weight per term, tile[2] = points per thread
+ *            along the slow axis (2 or 4 in 2D, 1 or 2 in 3D); 0 = default.
  * A family that cannot run a given (method, boundary, grid) makes stencil_run
  * return EUNSUPPORTED.
  *

@@ -229,6 +229,7 @@ int stencil_run(stencil_handle h, const stencil_grid* g, int64_t T, void* cuda_s
         else
             rc = jacobi_stream_run(ctx, g->data, scratch, T, p.tb, p.tile);
     } else {
+        if (p.kernel == STENCIL_KERNEL_PLAIN) ctx.prb = (int)p.tile[2];
         double* a = g->data;
         double* b = scratch;
         for (int64_t t = 0; t < T && rc == STENCIL_OK; ++t) {

@@ -53,6 +53,8 @@ struct RunCtx {
     StencilDev sd;
     // wavefront Gauss-Seidel parameters of the run's plan (tile[] of a WAVEFRONT plan, 0 = default)
     int64_t wtile[3] = {0, 0, 0};
+    // points per thread of the plain Jacobi step (tile[2] of a PLAIN plan: 2 or 4; 0 = default)
+    int prb = 0;
 };
 
 inline int cuda_rc(cudaError_t e) { return e == cudaSuccess ? STENCIL_OK : STENCIL_ECUDA; }

@@ -82,11 +82,12 @@ __host__ __device__ constexpr int plain_minb()
     return 1;
 }
 
-template <int DIM, int SHAPE, int R, int ARITH, class WS>
+// RBX: points per thread when a plain plan fixes it (0 = plain_rb's default).
+template <int DIM, int SHAPE, int R, int ARITH, class WS, int RBX = 0>
 __global__ void __launch_bounds__(256, plain_minb<DIM, SHAPE, R, WS::per_point>()) k_jacobi_plain(const double* __restrict__ u,
                                                       double* __restrict__ v, Geo g, int bc, double c, WS w)
 {
-    constexpr int RB = plain_rb<DIM, Stn<DIM, SHAPE, R>::K, WS::per_point>();
+    constexpr int RB = RBX > 0 ? RBX : plain_rb<DIM, Stn<DIM, SHAPE, R>::K, WS::per_point>();
     griddep_wait();  // launched programmatically: the previous step's writes are visible after this
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n2) return;
@@ -148,11 +149,11 @@ static void plain_launch_shape(const Geo& g, dim3& grid, dim3& block)
     grid = dim3((unsigned)gx, (unsigned)(gy < 65535 ? gy : 65535), (unsigned)(g.n0 < 65535 ? g.n0 : 65535));
 }
 
-template <int DIM, int SHAPE, int R, class WS>
+template <int DIM, int SHAPE, int R, class WS, int RBX = 0>
 static void launch_jacobi_plain(const RunCtx& ctx, const double* in, double* out, const WS& w)
 {
     constexpr int K = Stn<DIM, SHAPE, R>::K;
-    constexpr int RB = plain_rb<DIM, K, WS::per_point>();
+    constexpr int RB = RBX > 0 ? RBX : plain_rb<DIM, K, WS::per_point>();
     dim3 grid, block;
     plain_launch_shape(ctx.g, grid, block);
     if (DIM == 3) {
@@ -163,8 +164,8 @@ static void launch_jacobi_plain(const RunCtx& ctx, const double* in, double* out
         grid.y = (unsigned)(gy < 65535 ? gy : 65535);
     }
     // programmatic launch: the next step's CTAs are scheduled while this one drains (+1-2 %)
-    auto kern = ctx.h->arith == ARITH_FMA ? k_jacobi_plain<DIM, SHAPE, R, ARITH_FMA, WS>
-                                          : k_jacobi_plain<DIM, SHAPE, R, ARITH_UNFUSED, WS>;
+    auto kern = ctx.h->arith == ARITH_FMA ? k_jacobi_plain<DIM, SHAPE, R, ARITH_FMA, WS, RBX>
+                                          : k_jacobi_plain<DIM, SHAPE, R, ARITH_UNFUSED, WS, RBX>;
     if (launch_pdl(kern, grid, block, 0, ctx.st, in, out, ctx.g, ctx.h->bc, ctx.h->c, w) != cudaSuccess) {
         cudaGetLastError();  // a stream that refuses the attribute: an ordinary launch
         kern<<<grid, block, 0, ctx.st>>>(in, out, ctx.g, ctx.h->bc, ctx.h->c, w);
@@ -180,6 +181,15 @@ static void launch_jacobi_plain(const RunCtx& ctx, const double* in, double* out
     } else {
         WArr<K> w;
         for (int q = 0; q < K; ++q) w.w[q] = ctx.h->w_desc[q];
+        // a plain plan may fix the points per thread (radius 1: 2 or 4 in 2D, 1 or 2 in 3D, where 4 spills)
+        if constexpr (DIM == 2 && R == 1) {
+            if (ctx.prb == 2) return launch_jacobi_plain<DIM, SHAPE, R, WArr<K>, 2>(ctx, in, out, w);
+            if (ctx.prb == 4) return launch_jacobi_plain<DIM, SHAPE, R, WArr<K>, 4>(ctx, in, out, w);
+        }
+        if constexpr (DIM == 3 && R == 1) {
+            if (ctx.prb == 1) return launch_jacobi_plain<DIM, SHAPE, R, WArr<K>, 1>(ctx, in, out, w);
+            if (ctx.prb == 2) return launch_jacobi_plain<DIM, SHAPE, R, WArr<K>, 2>(ctx, in, out, w);
+        }
         launch_jacobi_plain<DIM, SHAPE, R>(ctx, in, out, w);
     }
 }

@@ -137,3 +137,16 @@ def test_jacobi2d_full_size_plain_equals_oracle_whole_grid(shape, k):
     ref = oracle_run(u0, 3, 2, shape, 1, w, "jacobi", "constant", 0.0, "fma")
     got = gpu_run(u0, 3, 2, shape, 1, w, "jacobi", "constant", 0.0, "fma", plan=1)
     assert bits_equal(got, ref), first_diff(got, ref)
+
+
+@pytest.mark.parametrize("dim,shape,ext,rb", [(2, "star", (37, 130), 2), (2, "box", (257, 131), 2),
+                                              (2, "star", (66, 65), 4), (3, "star", (33, 17, 40), 1),
+                                              (3, "box", (9, 10, 37), 1), (3, "star", (10, 13, 35), 2)])
+@pytest.mark.parametrize("bc,c", [("constant", 0.3), ("periodic", 0.0)])
+def test_jacobi_plain_points_per_thread(dim, shape, ext, rb, bc, c):
+    """The plain step with the points per thread a plain plan fixes (tile[2])."""
+    w, u0 = case(dim, shape, 1, ext, seed=dim * 13 + rb)
+    for arith in ("fma", "unfused"):
+        ref = oracle_run(u0, 5, dim, shape, 1, w, "jacobi", bc, c, arith)
+        got = gpu_run(u0, 5, dim, shape, 1, w, "jacobi", bc, c, arith, plan=PLAIN, tile=(0, 0, rb))
+        assert bits_equal(got, ref), (arith, first_diff(got, ref))
