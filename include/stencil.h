@@ -54,8 +54,8 @@ extern "C" {
 #define STENCIL_ENOMEM (-3)       /* device allocation failed */
 #define STENCIL_ECUDA (-4)        /* a CUDA call or kernel launch failed */
 #define STENCIL_ETIMEOUT (-5)     /* a device-side bounded wait gave up */
-#define STENCIL_EBOUNDS (-6)      /* a device-side index check failed (reserved: no kernel of this
-                                     build checks indices at run time; none reports it) */
+#define STENCIL_EBOUNDS (-6)      /* a device-side index check failed (checked build only: see
+                                     stencil_checked_build) */
 
 /* Stencil shape (Section 1 taxonomy). */
 #define STENCIL_STAR 0
@@ -230,7 +230,11 @@ int stencil_workspace_bytes(stencil_handle h, const stencil_grid* g, size_t* byt
 /*
  * Synchronise stream, then return and clear the handle's device status:
  * STENCIL_OK, STENCIL_ETIMEOUT or STENCIL_EBOUNDS (or ECUDA if the
- * synchronisation itself failed).
+ * synchronisation itself failed). In the checked build it also reads and
+ * clears the library's index-check fault records (process-wide, so a fault
+ * of any handle's kernel is reported by the next call, whichever handle it
+ * names) and answers STENCIL_EBOUNDS if one is set; bounds take precedence
+ * over a time-out.
  */
 int stencil_status(stencil_handle h, void* cuda_stream);
 
@@ -265,6 +269,27 @@ uint64_t stencil_launch_count(void);
  * such a run are unspecified. Nothing faults, traps or hangs.
  */
 int stencil_debug_inject_stall(stencil_handle h, int64_t unit, int spin);
+
+/*
+ * 1 if this library is the checked build, else 0. The checked build (the same
+ * sources compiled with -DSTENCIL_CHECKED into libgb300stencil_checked.so) tests
+ * every index the stencil kernels form into a grid, a coefficient field, a
+ * tile-flag table or a staged shared-memory tile (and that the staged tiles fit
+ * the launch's shared memory) before the access; a failing test skips the
+ * access and records the index, and stencil_status then returns
+ * STENCIL_EBOUNDS. It stands in for a memory checker on small cases: the
+ * results are otherwise bit-identical to the normal build's.
+ */
+int stencil_checked_build(void);
+
+/*
+ * Index-check test hook (no counterpart in the paper): one device thread on
+ * stream tests index i against extent n with the checked build's index check
+ * and touches no memory. In the checked build an i outside [0, n) makes the
+ * next stencil_status() return STENCIL_EBOUNDS; the normal build tests
+ * nothing. Returns STENCIL_ECUDA if the launch fails.
+ */
+int stencil_debug_check_index(int64_t i, int64_t n, void* cuda_stream);
 
 /*
  * Jacobi run that allocates nothing (the paper has no counterpart; this is a

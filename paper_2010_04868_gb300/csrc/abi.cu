@@ -41,6 +41,32 @@ int check_grid(const stencil_handle_s* h, const stencil_grid* g)
     return STENCIL_OK;
 }
 
+#ifdef STENCIL_CHECKED
+// The fault-word readers of the library's translation units (checked build); each unit adds its own
+// while the library loads.
+static std::vector<unsigned long long (*)()>& chk_readers()
+{
+    static std::vector<unsigned long long (*)()> v;
+    return v;
+}
+
+void chk_register(unsigned long long (*take)()) { chk_readers().push_back(take); }
+
+// Read and clear every unit's fault word; true if any index check failed since the last call.
+static bool chk_take_all()
+{
+    bool any = false;
+    for (auto f : chk_readers()) any |= f() != 0;
+    return any;
+}
+#endif
+
+__global__ void k_check_index(int64_t i, int64_t n)
+{
+    const bool ok = GBST_IN(i, n);
+    (void)ok;
+}
+
 }  // namespace gbst
 
 // Canonical offsets (lexicographic, slowest axis first), padded to 3 components.
@@ -256,6 +282,9 @@ int stencil_status(stencil_handle h, void* cuda_stream)
     int s = 0;
     if (cudaMemcpy(&s, h->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return STENCIL_ECUDA;
     if (s != DEV_OK && cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) return STENCIL_ECUDA;
+#ifdef STENCIL_CHECKED
+    if (chk_take_all()) return STENCIL_EBOUNDS;
+#endif
     if (s == DEV_TIMEOUT) return STENCIL_ETIMEOUT;
     if (s == DEV_BOUNDS) return STENCIL_EBOUNDS;
     return STENCIL_OK;
@@ -314,6 +343,22 @@ int stencil_debug_inject_stall(stencil_handle h, int64_t unit, int spin)
     h->debug_stall_tile = unit;
     h->debug_spin = spin;
     return STENCIL_OK;
+}
+
+int stencil_checked_build(void)
+{
+#ifdef STENCIL_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int stencil_debug_check_index(int64_t i, int64_t n, void* cuda_stream)
+{
+    k_check_index<<<1, 1, 0, (cudaStream_t)cuda_stream>>>(i, n);
+    g_launches++;
+    return cuda_rc(cudaGetLastError());
 }
 
 }  // extern "C"

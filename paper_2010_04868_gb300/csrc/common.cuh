@@ -28,6 +28,62 @@ enum { ARITH_FMA = 0, ARITH_UNFUSED = 1 };
 // Device status word values (mirrored by the C ABI's negative codes).
 enum { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BOUNDS = 2 };
 
+// Checked build (compiled with -DSTENCIL_CHECKED into its own library): every
+// index the stencil kernels form into a grid, a coefficient field or a staged
+// shared-memory tile goes through GBST_IN(i, n), which tests 0 <= i < n. A
+// failing test skips the access (a load reads 0), and the first failing index
+// is kept in a fault word of the kernel's translation unit; stencil_status
+// reads and clears the fault words of every unit and answers STENCIL_EBOUNDS.
+// The fault words are process-wide: a fault shows in the next stencil_status
+// call, whichever handle it names. In the normal build GBST_IN is the
+// constant true and every guarded access compiles to the plain access.
+#ifdef STENCIL_CHECKED
+static __device__ unsigned long long chk_fault_word;
+
+__device__ __forceinline__ bool chk_in(int64_t i, int64_t n)
+{
+    if (i >= 0 && i < n) return true;
+    // bit 63 marks a fault; the low 62 bits keep the failing index (two's complement, truncated)
+    atomicCAS(&chk_fault_word, 0ull, (1ull << 63) | ((unsigned long long)i & ((1ull << 62) - 1)));
+    return false;
+}
+#define GBST_IN(i, n) ::gbst::chk_in((int64_t)(i), (int64_t)(n))
+
+// The library's registry of fault-word readers (abi.cu): each unit adds its own at load time.
+void chk_register(unsigned long long (*take)());
+
+static unsigned long long chk_take_fault_word()
+{
+    unsigned long long v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, chk_fault_word, sizeof(v)) != cudaSuccess) return 0;
+    if (v) cudaMemcpyToSymbol(chk_fault_word, &zero, sizeof(zero));
+    return v;
+}
+static const int chk_registered = (chk_register(&chk_take_fault_word), 0);
+#else
+#define GBST_IN(i, n) true
+#endif
+
+// Bytes of dynamic shared memory this CTA was launched with.
+__device__ __forceinline__ uint32_t dyn_smem_bytes()
+{
+    uint32_t v;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+
+// Guarded element access: a[i] for 0 <= i < n; the checked build tests the index first.
+template <class T>
+__device__ __forceinline__ T ld_in(const T* a, int64_t i, int64_t n)
+{
+    return GBST_IN(i, n) ? a[i] : T(0);
+}
+template <class T>
+__device__ __forceinline__ void st_in(T* a, int64_t i, int64_t n, T v)
+{
+    if (GBST_IN(i, n)) a[i] = v;
+}
+
 // Extents padded to three dimensions, slowest first (a 1D grid is 1 x 1 x N).
 struct Geo {
     int64_t n0, n1, n2;
@@ -115,7 +171,10 @@ struct WField {
     static constexpr bool per_point = true;
     const double* f;
     int64_t n;
-    __device__ __forceinline__ double at(int q, int64_t p) const { return __ldg(f + (int64_t)(K - 1 - q) * n + p); }
+    __device__ __forceinline__ double at(int q, int64_t p) const
+    {
+        return GBST_IN(p, n) ? __ldg(f + (int64_t)(K - 1 - q) * n + p) : 0.0;
+    }
 };
 
 template <int ARITH>
@@ -144,7 +203,7 @@ __device__ __forceinline__ double fetch_bc(const double* u, int64_t i, int64_t j
     } else if (i < 0 || i >= g.n0 || j < 0 || j >= g.n1 || k < 0 || k >= g.n2) {
         return c;
     }
-    return u[(i * g.n1 + j) * g.n2 + k];
+    return ld_in(u, (i * g.n1 + j) * g.n2 + k, g.n0 * g.n1 * g.n2);
 }
 
 // Programmatic dependent launch: a kernel launched with the programmatic
@@ -173,16 +232,18 @@ __device__ __forceinline__ double update_bc(const double* u, int64_t i, int64_t 
     return acc;
 }
 
-// Full update at linear index p whose every neighbour is inside the grid.
+// Full update at linear index p whose every neighbour is inside the grid (or
+// the staged tile) u of n elements.
 template <int DIM, int SHAPE, int R, int ARITH, bool RO, class WS>
-__device__ __forceinline__ double update_interior(const double* u, int64_t p, int64_t s0, int64_t s1, const WS& w)
+__device__ __forceinline__ double update_interior(const double* u, int64_t p, int64_t s0, int64_t s1, const WS& w,
+                                                  int64_t n)
 {
     using S = Stn<DIM, SHAPE, R>;
     double v[S::K];
 #pragma unroll
     for (int q = 0; q < S::K; ++q) {
-        const double* a = u + p + S::o(q, 0) * s0 + S::o(q, 1) * s1 + S::o(q, 2);
-        v[q] = RO ? __ldg(a) : *a;
+        const int64_t a = p + S::o(q, 0) * s0 + S::o(q, 1) * s1 + S::o(q, 2);
+        v[q] = GBST_IN(a, n) ? (RO ? __ldg(u + a) : u[a]) : 0.0;
     }
     double acc = __dmul_rn(w.at(0, p), v[0]);
 #pragma unroll
@@ -204,7 +265,9 @@ __device__ __forceinline__ double update_rt(const double* u, int64_t i, int64_t 
             int q = q0 + t;
             if (q < s.K) {
                 v[t] = fetch_bc(u, i + s.off[3 * q], j + s.off[3 * q + 1], k + s.off[3 * q + 2], g, s.bc, s.c);
-                w[t] = s.field ? __ldg(s.field + (int64_t)(s.K - 1 - q) * s.npts + (i * g.n1 + j) * g.n2 + k) : s.w[q];
+                const int64_t p = (i * g.n1 + j) * g.n2 + k;
+                w[t] = s.field ? (GBST_IN(p, s.npts) ? __ldg(s.field + (int64_t)(s.K - 1 - q) * s.npts + p) : 0.0)
+                               : s.w[q];
             }
         }
 #pragma unroll

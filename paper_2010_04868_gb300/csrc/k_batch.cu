@@ -138,14 +138,14 @@ __device__ double point_bc(const double* u, int64_t i, int64_t j, int64_t k, con
 }
 
 template <int ARITH>
-__device__ double point_lin(const double* u, int64_t p, const long long* lo, const double* sw, int K)
+__device__ double point_lin(const double* u, int64_t p, const long long* lo, const double* sw, int K, int64_t n)
 {
     double acc = 0.0;
     for (int q0 = 0; q0 < K; q0 += 8) {
         double v[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t)
-            if (q0 + t < K) v[t] = u[p + lo[q0 + t]];
+            if (q0 + t < K) v[t] = ld_in(u, p + lo[q0 + t], n);
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             const int q = q0 + t;
@@ -219,8 +219,9 @@ __device__ __noinline__ void unit_jplain_sp(const BProb& P, int64_t ph, int64_t 
     for_jacobi_unit<!(DIM == 3 && SHAPE == BOX)>(P, u, [&](int64_t i, int64_t j, int64_t k, int64_t p) {
         const bool in = (DIM < 3 || (i >= 1 && i < P.g.n0 - 1)) && (DIM < 2 || (j >= 1 && j < P.g.n1 - 1)) &&
                         k >= 1 && k < P.g.n2 - 1;
-        dst[p] = in ? update_interior<DIM, SHAPE, 1, ARITH, false>(src, p, s0, s1, WPtr{sw})
-                    : update_bc<DIM, SHAPE, 1, ARITH>(src, i, j, k, P.g, P.bc, P.c, WPtr{sw});
+        st_in(dst, p, P.g.n0 * s0,
+              in ? update_interior<DIM, SHAPE, 1, ARITH, false>(src, p, s0, s1, WPtr{sw}, P.g.n0 * s0)
+                 : update_bc<DIM, SHAPE, 1, ARITH>(src, i, j, k, P.g, P.bc, P.c, WPtr{sw}));
     });
 }
 
@@ -233,7 +234,9 @@ __device__ __noinline__ void unit_jplain_rt(const BProb& P, int64_t ph, int64_t 
     for (int q = threadIdx.x; q < P.K; q += BT) lo[q] = (long long)so[3 * q] * n12 + so[3 * q + 1] * P.g.n2 + so[3 * q + 2];
     __syncthreads();
     for_jacobi_unit(P, u, [&](int64_t i, int64_t j, int64_t k, int64_t p) {
-        dst[p] = interior(P, i, j, k) ? point_lin<ARITH>(src, p, lo, sw, P.K) : point_bc<ARITH>(src, i, j, k, P, sw, so);
+        const int64_t np = P.g.n0 * n12;
+        st_in(dst, p, np,
+              interior(P, i, j, k) ? point_lin<ARITH>(src, p, lo, sw, P.K, np) : point_bc<ARITH>(src, i, j, k, P, sw, so));
     });
 }
 
@@ -249,6 +252,8 @@ __device__ __noinline__ void unit_jblock(const BProb& P, int64_t ph, int64_t uni
     const int64_t region = (int64_t)P.E0 * P.E1 * P.E2;
     double* A = sm;
     double* B = sm + ((region + 31) & ~int64_t(31));
+    // checked build: both staged buffers inside the launch's dynamic shared memory (uniform per CTA)
+    if (!GBST_IN(((region + 31) & ~int64_t(31)) + region - 1, (int64_t)(dyn_smem_bytes() / 8))) return;
     const int64_t st1 = P.E2, st0 = (int64_t)P.E1 * P.E2;
     for (int q = threadIdx.x; q < P.K; q += BT) lo[q] = (long long)so[3 * q] * st0 + so[3 * q + 1] * st1 + so[3 * q + 2];
     for (int64_t idx = threadIdx.x; idx < region; idx += BT) {
@@ -272,7 +277,7 @@ __device__ __noinline__ void unit_jblock(const BProb& P, int64_t ph, int64_t uni
                 if (i < 0 || i >= P.g.n0 || j < 0 || j >= P.g.n1 || k < 0 || k >= P.g.n2) continue;
             }
             const int64_t p = s0 * st0 + s1 * st1 + s2;
-            d[p] = point_lin<ARITH>(s, p, lo, sw, P.K);
+            st_in(d, p, region, point_lin<ARITH>(s, p, lo, sw, P.K, region));
         }
         __syncthreads();
         double* t = s;
@@ -284,7 +289,8 @@ __device__ __noinline__ void unit_jblock(const BProb& P, int64_t ph, int64_t uni
         const int l2 = (int)(idx % P.B2), l1 = (int)((idx / P.B2) % P.B1), l0 = (int)(idx / ((int64_t)P.B2 * P.B1));
         const int64_t i = T0 * P.B0 + l0, j = T1 * P.B1 + l1, k = T2 * P.B2 + l2;
         if (i < P.g.n0 && j < P.g.n1 && k < P.g.n2)
-            dst[(i * P.g.n1 + j) * P.g.n2 + k] = s[(l0 + P.h0) * st0 + (l1 + P.h1) * st1 + (l2 + P.h2)];
+            st_in(dst, (i * P.g.n1 + j) * P.g.n2 + k, P.g.n0 * P.g.n1 * P.g.n2,
+                  ld_in(s, (l0 + P.h0) * st0 + (l1 + P.h1) * st1 + (l2 + P.h2), region));
     }
 }
 
@@ -329,11 +335,12 @@ __device__ __noinline__ void unit_gstile(const BProb& P, int64_t ph, int64_t uni
             const int64_t p = i * s0 + j * s1 + k;
             double r;
             if (SPEC)
-                r = (in01 && k >= 1 && k < P.g.n2 - 1) ? update_interior<DIM, SHAPE, 1, ARITH, false>(u, p, s0, s1, WPtr{sw})
-                                                       : update_bc<DIM, SHAPE, 1, ARITH>(u, i, j, k, P.g, P.bc, P.c, WPtr{sw});
+                r = (in01 && k >= 1 && k < P.g.n2 - 1)
+                        ? update_interior<DIM, SHAPE, 1, ARITH, false>(u, p, s0, s1, WPtr{sw}, P.g.n0 * s0)
+                        : update_bc<DIM, SHAPE, 1, ARITH>(u, i, j, k, P.g, P.bc, P.c, WPtr{sw});
             else
                 r = point_bc<ARITH>(u, i, j, k, P, sw, so);
-            u[p] = r;
+            st_in(u, p, P.g.n0 * s0, r);
         }
         __syncthreads();
     }

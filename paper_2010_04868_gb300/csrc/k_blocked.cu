@@ -88,6 +88,8 @@ __global__ void __launch_bounds__(256) k_jacobi_blocked(const __grid_constant__ 
     const int64_t region = (int64_t)b.E0 * b.E1 * b.E2;
     double* bufA = sm;
     double* bufB = sm + ((region + 31) & ~int64_t(31));
+    // checked build: both staged buffers inside the launch's dynamic shared memory (uniform per CTA)
+    if (!GBST_IN(((region + 31) & ~int64_t(31)) + region - 1, (int64_t)(dyn_smem_bytes() / 8))) return;
 
     // tile coordinates
     int64_t t = blockIdx.x;
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(256) k_jacobi_blocked(const __grid_constant__ 
             const int s2 = (int)(idx % b.E2);
             const int s1 = (int)((idx / b.E2) % b.E1);
             const int s0 = (int)(idx / ((int64_t)b.E2 * b.E1));
-            bufA[idx] = fetch_bc(in, g0 + s0, g1 + s1, g2 + s2, g, bc, c);
+            st_in(bufA, idx, region, fetch_bc(in, g0 + s0, g1 + s1, g2 + s2, g, bc, c));
         }
     }
     // cells outside the grid hold the boundary value in both buffers
@@ -162,8 +164,8 @@ __global__ void __launch_bounds__(256) k_jacobi_blocked(const __grid_constant__ 
             const int64_t j = g1 + (idx / b.E2) % b.E1;
             const int64_t k = g2 + idx % b.E2;
             if (i < 0 || i >= g.n0 || j < 0 || j >= g.n1 || k < 0 || k >= g.n2) {
-                bufA[idx] = c;
-                bufB[idx] = c;
+                st_in(bufA, idx, region, c);
+                st_in(bufB, idx, region, c);
             }
         }
     }
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(256) k_jacobi_blocked(const __grid_constant__ 
                 if (i < 0 || i >= g.n0 || j < 0 || j >= g.n1 || k < 0 || k >= g.n2) continue;
             }
             const int64_t p = s0 * st0 + s1 * st1 + s2;
-            dst[p] = update_interior<DIM, SHAPE, R, ARITH, false>(src, p, st0, st1, w);
+            st_in(dst, p, region, update_interior<DIM, SHAPE, R, ARITH, false>(src, p, st0, st1, w, region));
         }
         __syncthreads();
         double* tmp = src;
@@ -205,7 +207,8 @@ __global__ void __launch_bounds__(256) k_jacobi_blocked(const __grid_constant__ 
         const int l0 = (int)(idx / ((int64_t)b.B2 * b.B1));
         const int64_t i = T0 * b.B0 + l0, j = T1 * b.B1 + l1, k = T2 * b.B2 + l2;
         if (i < g.n0 && j < g.n1 && k < g.n2)
-            out[(i * g.n1 + j) * g.n2 + k] = src[(l0 + b.h0) * st0 + (l1 + b.h1) * st1 + (l2 + b.h2 + pad2)];
+            st_in(out, (i * g.n1 + j) * g.n2 + k, g.n0 * g.n1 * g.n2,
+                  ld_in(src, (l0 + b.h0) * st0 + (l1 + b.h1) * st1 + (l2 + b.h2 + pad2), region));
     }
 }
 

@@ -292,14 +292,14 @@ __device__ __forceinline__ void dia_import(const DiaGeo& G, const DiaTile& t, in
 // sum keeps the descending canonical order and rounding of update_interior.
 template <int DIM, int SHAPE, int R, int ARITH, class WS>
 __device__ __forceinline__ void update_pair(const double* src, int p, int fs0, int fs1, const WS& w, double& va,
-                                            double& vb)
+                                            double& vb, int n)
 {
     using S = Stn<DIM, SHAPE, R>;
     double a[S::K], b[S::K];
 #pragma unroll
     for (int q = 0; q < S::K; ++q) {
-        a[q] = src[p + S::o(q, 0) * fs0 + S::o(q, 1) * fs1 + S::o(q, 2)];
-        b[q] = src[p + S::o(q, 0) * fs0 + (S::o(q, 1) + 1) * fs1 + S::o(q, 2)];
+        a[q] = ld_in(src, p + S::o(q, 0) * fs0 + S::o(q, 1) * fs1 + S::o(q, 2), n);
+        b[q] = ld_in(src, p + S::o(q, 0) * fs0 + (S::o(q, 1) + 1) * fs1 + S::o(q, 2), n);
     }
     double acc = __dmul_rn(w.at(0, 0), a[0]), acb = __dmul_rn(w.at(0, 0), b[0]);
 #pragma unroll
@@ -319,7 +319,10 @@ __global__ void __launch_bounds__(256, (DIM == 2 && SHAPE == STAR && R == 1) ? 4
     const int F = G.fw[0] * G.fw[1] * G.fw[2];
     double* const bufA = sm;
     double* const bufB = sm + ((F + 1) & ~1);
+    // checked build: both level buffers inside the launch's dynamic shared memory (uniform per CTA)
+    if (!GBST_IN(((F + 1) & ~1) + F - 1, (int64_t)(dyn_smem_bytes() / 8))) return;
     auto buf = [&](int k) { return (k & 1) ? bufB : bufA; };  // level k's buffer, no local-memory array
+    const int64_t NP = (int64_t)G.N[0] * G.N[1] * G.N[2];
     const int fs1 = G.fw[2], fs0 = G.fw[1] * G.fw[2];
     DiaTile t;
     dia_tile(G, phase, R, t);
@@ -346,7 +349,8 @@ __global__ void __launch_bounds__(256, (DIM == 2 && SHAPE == STAR && R == 1) ? 4
         for (int i = threadIdx.x; i < cnt; i += nthr, it.next()) {
             const int q0 = L[0] + it.x0, q1 = L[1] + it.x1, q2 = L[2] + it.x2;
             const int64_t gi = ((int64_t)wrapn(q0, G.N[0]) * G.N[1] + wrapn(q1, G.N[1])) * G.N[2] + wrapn(q2, G.N[2]);
-            cp_async8(bufA + (q0 - t.f0[0]) * fs0 + (q1 - t.f0[1]) * fs1 + (q2 - t.f0[2]), u + gi);
+            const int l = (q0 - t.f0[0]) * fs0 + (q1 - t.f0[1]) * fs1 + (q2 - t.f0[2]);
+            if (GBST_IN(l, F) && GBST_IN(gi, NP)) cp_async8(bufA + l, u + gi);
         }
     }
     // groups: {base, ring 0}, ring 1, ..., ring DIA_AHEAD-1 (empty groups past the band)
@@ -388,7 +392,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 && SHAPE == STAR && R == 1) ? 4
             const int L = isB ? lo - k * R : lo + (shL ? k * R : 0);
             const int U = isB ? (clip ? min(hi + k * R, N) : hi + k * R) : hi - k * R;
             for (int i = L - f0 + tid; i < U - f0; i += nthr)
-                dst[i] = update_interior<DIM, SHAPE, R, ARITH, false>(src, i, fs0, fs1, w);
+                st_in(dst, i, F, update_interior<DIM, SHAPE, R, ARITH, false>(src, i, fs0, fs1, w, F));
             cp_async_wait<DIA_AHEAD - 1>();  // ring k has landed
             __syncthreads();
         }
@@ -419,14 +423,14 @@ __global__ void __launch_bounds__(256, (DIM == 2 && SHAPE == STAR && R == 1) ? 4
                 it.next();
                 const int pb = base + it.x0 * fs0 + it.x1 * fs1 + it.x2;
                 it.next();
-                const double va = update_interior<DIM, SHAPE, R, ARITH, false>(src, pa, fs0, fs1, w);
-                const double vb = update_interior<DIM, SHAPE, R, ARITH, false>(src, pb, fs0, fs1, w);
-                dst[pa] = va;
-                dst[pb] = vb;
+                const double va = update_interior<DIM, SHAPE, R, ARITH, false>(src, pa, fs0, fs1, w, F);
+                const double vb = update_interior<DIM, SHAPE, R, ARITH, false>(src, pb, fs0, fs1, w, F);
+                st_in(dst, pa, F, va);
+                st_in(dst, pb, F, vb);
             }
             if (i < cnt) {
                 const int pa = base + it.x0 * fs0 + it.x1 * fs1 + it.x2;
-                dst[pa] = update_interior<DIM, SHAPE, R, ARITH, false>(src, pa, fs0, fs1, w);
+                st_in(dst, pa, F, update_interior<DIM, SHAPE, R, ARITH, false>(src, pa, fs0, fs1, w, F));
             }
             cp_async_wait<DIA_AHEAD - 1>();  // ring k has landed
             __syncthreads();
@@ -441,11 +445,11 @@ __global__ void __launch_bounds__(256, (DIM == 2 && SHAPE == STAR && R == 1) ? 4
             const int pa = base + it.x0 * fs0 + y * fs1 + it.x2;
             if (y + 1 < e1) {
                 double va, vb;
-                update_pair<DIM, SHAPE, R, ARITH>(src, pa, fs0, fs1, w, va, vb);
-                dst[pa] = va;
-                dst[pa + fs1] = vb;
+                update_pair<DIM, SHAPE, R, ARITH>(src, pa, fs0, fs1, w, va, vb, F);
+                st_in(dst, pa, F, va);
+                st_in(dst, pa + fs1, F, vb);
             } else {
-                dst[pa] = update_interior<DIM, SHAPE, R, ARITH, false>(src, pa, fs0, fs1, w);
+                st_in(dst, pa, F, update_interior<DIM, SHAPE, R, ARITH, false>(src, pa, fs0, fs1, w, F));
             }
         }
         cp_async_wait<DIA_AHEAD - 1>();  // ring k has landed
@@ -465,7 +469,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 && SHAPE == STAR && R == 1) ? 4
         for (int i = threadIdx.x; i < cnt; i += nthr, it.next()) {
             const int q0 = L[0] + it.x0, q1 = L[1] + it.x1, q2 = L[2] + it.x2;
             const int64_t gi = ((int64_t)wrapn(q0, G.N[0]) * G.N[1] + wrapn(q1, G.N[1])) * G.N[2] + wrapn(q2, G.N[2]);
-            u[gi] = b[(q0 - t.f0[0]) * fs0 + (q1 - t.f0[1]) * fs1 + (q2 - t.f0[2])];
+            st_in(u, gi, NP, ld_in(b, (q0 - t.f0[0]) * fs0 + (q1 - t.f0[1]) * fs1 + (q2 - t.f0[2]), F));
         }
     }
 }
@@ -585,6 +589,9 @@ __global__ void __launch_bounds__(512) k_jacobi_hex1d(double* __restrict__ u, He
     double* const arb = B1 + G.fwB;         // H x 2r: A's right band per level
     double* const rvb = arb + G.H * 2 * R;  // 8 x 2r: the next period's A left band, ring of levels
     double* const alb = rvb + 8 * 2 * R;    // H x 2r: A's left band per level, staged for the comm warp
+    const int nAB = 2 * G.fwA + 2 * G.fwB;  // the four level buffers
+    // checked build: every staged array inside the launch's dynamic shared memory (uniform per CTA)
+    if (!GBST_IN((int64_t)nAB + (2 * G.H + 8) * 2 * R - 1, (int64_t)(dyn_smem_bytes() / 8))) return;
     auto Ab = [&](int g) { return (g & 1) ? A1 : A0; };
     auto Bb = [&](int g) { return (g & 1) ? B1 : B0; };
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -642,7 +649,7 @@ __global__ void __launch_bounds__(512) k_jacobi_hex1d(double* __restrict__ u, He
                     const bool inA = i < nA;
                     const int ps = inA ? oAs + aL + i : oBs + bL + i - nA;
                     const int pd = inA ? oAd + aL + i : oBd + bL + i - nA;
-                    sm[pd] = update_interior<1, STAR, R, ARITH, false>(sm, ps, 0, 0, w);
+                    st_in(sm, pd, nAB, update_interior<1, STAR, R, ARITH, false>(sm, ps, 0, 0, w, nAB));
                 }
                 // A's bands of level s - 1: the left one staged for the previous period, the right one for B
                 if (kx < h && tid < 4 * R) {

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256, plain_minb<DIM, SHAPE, R, WS::per_point>(
     griddep_wait();  // launched programmatically: the previous step's writes are visible after this
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n2) return;
-    const int64_t s1 = g.n2, s0 = g.n1 * g.n2;
+    const int64_t s1 = g.n2, s0 = g.n1 * g.n2, np = g.n0 * s0;
     const bool kin = k >= R && k < g.n2 - R;
     if (DIM == 3) {
         for (int64_t i0 = (int64_t)blockIdx.z * RB; i0 < g.n0; i0 += (int64_t)gridDim.z * RB)
@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(256, plain_minb<DIM, SHAPE, R, WS::per_point>(
                     if (i < g.n0) {
                         const int64_t p = i * s0 + j * s1 + k;
                         const bool in = kin && jin && i >= R && i < g.n0 - R;
-                        v[p] = in ? update_interior<DIM, SHAPE, R, ARITH, true>(u, p, s0, s1, w)
-                                  : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w);
+                        st_in(v, p, np, in ? update_interior<DIM, SHAPE, R, ARITH, true>(u, p, s0, s1, w, np)
+                                           : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w));
                     }
                 }
             }
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(256, plain_minb<DIM, SHAPE, R, WS::per_point>(
                 if (j < g.n1) {
                     const int64_t p = j * s1 + k;
                     const bool in = kin && (DIM < 2 || (j >= R && j < g.n1 - R));
-                    v[p] = in ? update_interior<DIM, SHAPE, R, ARITH, true>(u, p, s0, s1, w)
-                              : update_bc<DIM, SHAPE, R, ARITH>(u, 0, j, k, g, bc, c, w);
+                    st_in(v, p, np, in ? update_interior<DIM, SHAPE, R, ARITH, true>(u, p, s0, s1, w, np)
+                                       : update_bc<DIM, SHAPE, R, ARITH>(u, 0, j, k, g, bc, c, w));
                 }
             }
         }
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256) k_jacobi_plain_rt(const double* __restric
     for (int64_t i = blockIdx.z; i < g.n0; i += gridDim.z)
         for (int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; j < g.n1;
              j += (int64_t)gridDim.y * blockDim.y)
-            v[(i * g.n1 + j) * g.n2 + k] = update_rt<ARITH>(u, i, j, k, g, s);
+            st_in(v, (i * g.n1 + j) * g.n2 + k, g.n0 * g.n1 * g.n2, update_rt<ARITH>(u, i, j, k, g, s));
 }
 
 static void plain_launch_shape(const Geo& g, dim3& grid, dim3& block)
@@ -229,8 +229,8 @@ __global__ void k_gs1d_serial(double* u, int64_t n, int bc, double c, WS w)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     auto fetch = [&](int64_t x) -> double {
-        if (x >= 0 && x < n) return u[x];
-        if (bc == BC_PERIODIC) return u[x < 0 ? x + n : x - n];
+        if (x >= 0 && x < n) return ld_in(u, x, n);
+        if (bc == BC_PERIODIC) return ld_in(u, x < 0 ? x + n : x - n, n);
         return c;
     };
     double win[2 * R + 1];
@@ -241,7 +241,7 @@ __global__ void k_gs1d_serial(double* u, int64_t n, int bc, double c, WS w)
         double acc = __dmul_rn(w.at(0, x), win[2 * R]);
 #pragma unroll
         for (int q = 1; q <= 2 * R; ++q) acc = acc_step<ARITH>(acc, w.at(q, x), win[2 * R - q]);
-        u[x] = acc;
+        st_in(u, x, n, acc);
 #pragma unroll
         for (int m = 0; m < 2 * R; ++m) win[m] = win[m + 1];
         win[R - 1] = acc;
@@ -256,7 +256,8 @@ __global__ void k_gs_serial_rt(double* u, Geo g, StencilDev s)
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     for (int64_t i = 0; i < g.n0; ++i)
         for (int64_t j = 0; j < g.n1; ++j)
-            for (int64_t k = 0; k < g.n2; ++k) u[(i * g.n1 + j) * g.n2 + k] = update_rt<ARITH>(u, i, j, k, g, s);
+            for (int64_t k = 0; k < g.n2; ++k)
+                st_in(u, (i * g.n1 + j) * g.n2 + k, g.n0 * g.n1 * g.n2, update_rt<ARITH>(u, i, j, k, g, s));
 }
 
 // Parallelogram tiles for a Gauss-Seidel sweep (the paper uses parallelogram
@@ -304,9 +305,10 @@ __global__ void __launch_bounds__(256) k_gs_tile(double* u, Geo g, int bc, doubl
         const int64_t k = kb + ls;
         if (owner && k >= 0 && k < g.n2) {
             const int64_t p = i * s0 + j * s1 + k;
-            double r = (in01 && k >= R && k < g.n2 - R) ? update_interior<DIM, SHAPE, R, ARITH, false>(u, p, s0, s1, w)
-                                                        : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w);
-            u[p] = r;
+            double r = (in01 && k >= R && k < g.n2 - R)
+                           ? update_interior<DIM, SHAPE, R, ARITH, false>(u, p, s0, s1, w, g.n0 * s0)
+                           : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w);
+            st_in(u, p, g.n0 * s0, r);
         }
         __syncthreads();
     }

@@ -123,6 +123,11 @@ __device__ __forceinline__ void stream_load(const CUtensorMap* tmap, const doubl
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             const uint32_t bar = bar_base + 8u * (uint32_t)(k % (STREAM_PF + 1));
             const uint32_t bytes = (uint32_t)(M * P * 8);
+            if (!GBST_IN((int64_t)(slot + M) * P - 1, (int64_t)sg.C0 * P)) {
+                // checked build: the box would overrun ring 0; complete the phase without a copy
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+                return;
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
             const uint32_t dst = s_u32(ring0 + (int64_t)slot * P);
@@ -157,10 +162,13 @@ __device__ __forceinline__ void stream_load(const CUtensorMap* tmap, const doubl
                 if (DIM == 3) gj = wrap_mod(gj, n1);
                 in_grid = true;
             }
-            double* d = ring0 + (int64_t)(slot + m) * P + jj * sg.W2 + x;
+            const int64_t di = (int64_t)(slot + m) * P + jj * sg.W2 + x;
+            if (!GBST_IN(di, (int64_t)sg.C0 * P)) continue;
+            double* d = ring0 + di;
             if (in_grid) {
-                const double* src = in + ((DIM == 3 ? zz * n1 + gj : zz) * g.n2 + gxx);
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s_u32(d)), "l"(src) : "memory");
+                const int64_t si = (DIM == 3 ? zz * n1 + gj : zz) * g.n2 + gxx;
+                if (!GBST_IN(si, g.n0 * g.n1 * g.n2)) continue;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s_u32(d)), "l"(in + si) : "memory");
             } else {
                 *d = c;
             }
@@ -180,6 +188,8 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_stream(const __grid_constant_
     extern __shared__ __align__(128) double sm[];
     __shared__ __align__(8) uint64_t bars[STREAM_PF + 1];
     const int P = sg.W1 * sg.W2;
+    // checked build: all rings inside the launch's dynamic shared memory (uniform per CTA)
+    if (!GBST_IN((int64_t)(sg.C0 + (TB - 1) * sg.C) * P - 1, (int64_t)(dyn_smem_bytes() / 8))) return;
     double* ring[TB];
     ring[0] = sm;
 #pragma unroll
@@ -224,7 +234,8 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_stream(const __grid_constant_
                 const int64_t gj = gj0 + jj;
                 if (xout || (DIM == 3 && (gj < 0 || gj >= n1)))
                     for (int s = 1; s < TB; ++s)
-                        for (int sl = 0; sl < sg.C; ++sl) ring[s][(int64_t)sl * P + jj * sg.W2 + x] = c;
+                        for (int sl = 0; sl < sg.C; ++sl)
+                            st_in(ring[s], (int64_t)sl * P + jj * sg.W2 + x, (int64_t)sg.C * P, c);
             }
         }
         __syncthreads();  // the rings are free (the previous segment is done) and the barriers initialised
@@ -263,7 +274,7 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_stream(const __grid_constant_
                         for (int jj = jb; jj < jb + sg.J; ++jj) {
                             const int64_t gj = gj0 + jj;
                             if (zout || xout || (DIM == 3 && (gj < 0 || gj >= n1)))
-                                ring[0][(int64_t)(slot + m) * P + jj * sg.W2 + x] = c;
+                                st_in(ring[0], (int64_t)(slot + m) * P + jj * sg.W2 + x, (int64_t)sg.C0 * P, c);
                         }
                     }
                 }
@@ -312,7 +323,7 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_stream(const __grid_constant_
                         const int co = cell + dj * sg.W2 + dx;
     #pragma unroll
                         for (int m = 0; m < M; ++m) {
-                            const double v = src[so[m + R + dz] + co];
+                            const double v = ld_in(src, (int64_t)so[m + R + dz] + co, (int64_t)Cin * P);
                             acc[m] = q == 0 ? __dmul_rn(w.w[0], v) : acc_step<ARITH>(acc[m], w.w[q], v);
                         }
                     }
@@ -322,7 +333,8 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_stream(const __grid_constant_
                         for (int m = 0; m < M; ++m) {
                             const int64_t y = y0 + m;
                             if (y < lo || y >= hi) continue;
-                            dst[oo[m] + cell] = (constant && (y < 0 || y >= nz)) ? c : acc[m];
+                            st_in(dst, (int64_t)oo[m] + cell, (int64_t)sg.C * P,
+                                  (constant && (y < 0 || y >= nz)) ? c : acc[m]);
                         }
                     } else {
                         // the last level: the output tile, inside the grid
@@ -334,7 +346,7 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_stream(const __grid_constant_
                         for (int m = 0; m < M; ++m) {
                             const int64_t y = y0 + m;
                             if (y < lo || y >= hi) continue;
-                            out[(DIM == 3 ? y * n1 + gj : y) * g.n2 + gx] = acc[m];
+                            st_in(out, (DIM == 3 ? y * n1 + gj : y) * g.n2 + gx, g.n0 * g.n1 * g.n2, acc[m]);
                         }
                     }
                 }

@@ -484,6 +484,22 @@ __device__ __forceinline__ bool wait_flag_ge(const int* f, int tag, int spin)
     return false;
 }
 
+// Flag f of a table of n flags; the checked build skips a wait or a release outside the table.
+__device__ __forceinline__ bool wait_flag_at(const int* flags, int64_t f, int64_t n, int tag, int spin)
+{
+    return GBST_IN(f, n) ? wait_flag(flags + f, tag, spin) : true;
+}
+
+__device__ __forceinline__ bool wait_flag_ge_at(const int* flags, int64_t f, int64_t n, int tag, int spin)
+{
+    return GBST_IN(f, n) ? wait_flag_ge(flags + f, tag, spin) : true;
+}
+
+__device__ __forceinline__ void release_flag_at(int* flags, int64_t f, int64_t n, int tag)
+{
+    if (GBST_IN(f, n)) st_release(flags + f, tag);
+}
+
 // Which window cells a point update reads: every cell for a box; for a star
 // the centre row in full and the other rows only above/below the points.
 template <int SHAPE, int R, int W>
@@ -533,7 +549,7 @@ __device__ __forceinline__ void lane_step(double* __restrict__ u, const Geo& g, 
 #pragma unroll
         for (int q = 1; q < St::K; ++q) acc = acc_step<ARITH>(acc, w.at(q, pw), v[q]);
         if (q2 >= 0 && q2 < g.n2) {
-            u[row + q2] = acc;
+            st_in(u, row + q2, g.n0 * g.n1 * g.n2, acc);
             win[DIM == 3 ? R : 0][R][m + R] = acc;  // newest value, read by the next points as a left neighbour
         }
     }
@@ -555,14 +571,14 @@ __global__ void __launch_bounds__(128) k_gs_wave(double* __restrict__ u, Geo g, 
         const int64_t fidx = ((b * wg.nI + I) * wg.nJ + J) * wg.nK + K;
         // predecessors: the three lower neighbours in this block, the shifted tile of the previous block
         bool ok = true;
-        if (I > 0) ok &= wait_flag(flags + fidx - wg.nJ * wg.nK, tag, wc.spin);
-        if (J > 0) ok &= wait_flag(flags + fidx - wg.nK, tag, wc.spin);
-        if (K > 0) ok &= wait_flag(flags + fidx - 1, tag, wc.spin);
+        if (I > 0) ok &= wait_flag_at(flags, fidx - wg.nJ * wg.nK, wg.ntiles, tag, wc.spin);
+        if (J > 0) ok &= wait_flag_at(flags, fidx - wg.nK, wg.ntiles, tag, wc.spin);
+        if (K > 0) ok &= wait_flag_at(flags, fidx - 1, wg.ntiles, tag, wc.spin);
         if (b > 0) {
             const int64_t pI = I + wg.dI < wg.nI - 1 ? I + wg.dI : wg.nI - 1;
             const int64_t pJ = J + wg.dJ < wg.nJ - 1 ? J + wg.dJ : wg.nJ - 1;
             const int64_t pK = K + wg.dK < wg.nK - 1 ? K + wg.dK : wg.nK - 1;
-            ok &= wait_flag(flags + (((b - 1) * wg.nI + pI) * wg.nJ + pJ) * wg.nK + pK, tag, wc.spin);
+            ok &= wait_flag_at(flags, (((b - 1) * wg.nI + pI) * wg.nJ + pJ) * wg.nK + pK, wg.ntiles, tag, wc.spin);
         }
         if (!ok && lane == 0) atomicExch(status, DEV_TIMEOUT);
         __syncwarp();
@@ -594,7 +610,7 @@ __global__ void __launch_bounds__(128) k_gs_wave(double* __restrict__ u, Geo g, 
         }
         if (lane == 0 && fidx != wc.stall) {
             __threadfence();
-            st_release(flags + fidx, tag);
+            release_flag_at(flags, fidx, wg.ntiles, tag);
         }
         __syncwarp();
     }
@@ -674,12 +690,12 @@ __global__ void __launch_bounds__(GD_THREADS) k_gs2d_dec(double* __restrict__ u,
             if (tk < wg.ntiles) {
                 decode_tile<2>(tk, pre, wg, b, I, J, K);
                 const int64_t fidx = (b * wg.nI + I) * wg.nJ + J;
-                if (I > 0) ok &= wait_flag(flags + fidx - wg.nJ, tag, wc.spin);
-                if (J > 0) ok &= wait_flag(flags + fidx - 1, tag, wc.spin);
+                if (I > 0) ok &= wait_flag_at(flags, fidx - wg.nJ, wg.ntiles, tag, wc.spin);
+                if (J > 0) ok &= wait_flag_at(flags, fidx - 1, wg.ntiles, tag, wc.spin);
                 if (b > 0) {
                     const int64_t pI = I + wg.dI < wg.nI - 1 ? I + wg.dI : wg.nI - 1;
                     const int64_t pJ = J + wg.dJ < wg.nJ - 1 ? J + wg.dJ : wg.nJ - 1;
-                    ok &= wait_flag(flags + ((b - 1) * wg.nI + pI) * wg.nJ + pJ, tag, wc.spin);
+                    ok &= wait_flag_at(flags, ((b - 1) * wg.nI + pI) * wg.nJ + pJ, wg.ntiles, tag, wc.spin);
                 }
             }
             nxt[0] = tk;
@@ -761,7 +777,7 @@ __global__ void __launch_bounds__(GD_THREADS) k_gs2d_dec(double* __restrict__ u,
             const int64_t fidx = (b * wg.nI + I) * wg.nJ + J;
             if (tid == 0 && fidx != wc.stall) {
                 __threadfence();
-                st_release(flags + fidx, tag);
+                release_flag_at(flags, fidx, wg.ntiles, tag);
             }
         }
         __syncthreads();
@@ -926,11 +942,11 @@ __global__ void __launch_bounds__(256) k_gs_sweepdag(double* __restrict__ u, Geo
                 if (sw > 0) {
                     int64_t pw[4];
                     const int np = sweep_dag_prev_waits<DIM, R>(t, g, T0, T1, TS, pw);
-                    for (int q = 0; q < np; ++q) ok &= wait_flag_ge(flags + pw[q], (int)sw, wc.spin);
+                    for (int q = 0; q < np; ++q) ok &= wait_flag_ge_at(flags, pw[q], t.sweep_units, (int)sw, wc.spin);
                 }
-                if (T0 > 0) ok &= wait_flag_ge(flags + f - t.nt1 * t.nts, tag, wc.spin);
-                if (T1 > 0) ok &= wait_flag_ge(flags + f - t.nts, tag, wc.spin);
-                if (TS > 0) ok &= wait_flag_ge(flags + f - 1, tag, wc.spin);
+                if (T0 > 0) ok &= wait_flag_ge_at(flags, f - t.nt1 * t.nts, t.sweep_units, tag, wc.spin);
+                if (T1 > 0) ok &= wait_flag_ge_at(flags, f - t.nts, t.sweep_units, tag, wc.spin);
+                if (TS > 0) ok &= wait_flag_ge_at(flags, f - 1, t.sweep_units, tag, wc.spin);
                 if (!ok) atomicExch(status, DEV_TIMEOUT);
                 __threadfence();
             }
@@ -947,15 +963,17 @@ __global__ void __launch_bounds__(256) k_gs_sweepdag(double* __restrict__ u, Geo
             const int64_t k = kb + ls;
             if (owner && k >= 0 && k < g.n2) {
                 const int64_t p = i * s0 + j * s1 + k;
-                u[p] = (in01 && k >= R && k < g.n2 - R) ? update_interior<DIM, SHAPE, R, ARITH, false>(u, p, s0, s1, w)
-                                                        : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w);
+                st_in(u, p, g.n0 * s0,
+                      (in01 && k >= R && k < g.n2 - R)
+                          ? update_interior<DIM, SHAPE, R, ARITH, false>(u, p, s0, s1, w, g.n0 * s0)
+                          : update_bc<DIM, SHAPE, R, ARITH>(u, i, j, k, g, bc, c, w));
             }
             __syncthreads();
         }
         if (threadIdx.x == 0) {
             const int64_t f = (s_T0 * t.nt1 + s_T1) * t.nts + s_TS;
             __threadfence();
-            if (s_sw * t.sweep_units + f != wc.stall) st_release(flags + f, (int)s_sw + 1);
+            if (s_sw * t.sweep_units + f != wc.stall) release_flag_at(flags, f, t.sweep_units, (int)s_sw + 1);
             atomicAdd(finished, 1ull);
         }
     }

@@ -27,13 +27,18 @@ STENCIL_KERNEL_AUTO, STENCIL_KERNEL_PLAIN, STENCIL_KERNEL_BLOCKED, STENCIL_KERNE
 STENCIL_KERNEL_DIAMOND = 4
 STENCIL_KERNEL_STREAM = 5
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgb300stencil.so")
+#: The library this module loads: the checked build (every kernel index tested before its access, a
+#: failing test reported as STENCIL_EBOUNDS) when the environment sets STENCIL_CHECKED=1, else the normal one.
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                        "libgb300stencil_checked.so" if os.environ.get("STENCIL_CHECKED") == "1"
+                        else "libgb300stencil.so")
 
 #: Every entry point that include/stencil.h declares.
 EXPORTS = ("stencil_create", "stencil_set_plan", "stencil_run", "stencil_run_batch", "stencil_workspace_bytes",
            "stencil_status", "stencil_destroy", "stencil_strerror", "stencil_run_host", "stencil_launch_count",
            "stencil_run_noalloc", "stencil_debug_inject_stall", "stencil_set_coeff_field", "stencil_get_plan",
-           "life_workspace_bytes", "life_run", "lcs_workspace_bytes", "lcs_run", "lcs_status")
+           "life_workspace_bytes", "life_run", "lcs_workspace_bytes", "lcs_run", "lcs_status",
+           "stencil_checked_build", "stencil_debug_check_index")
 
 #: Largest grid (points) stencil_run_noalloc accepts: its fixed workspace holds 2^21 doubles.
 NOALLOC_MAX_POINTS = 1 << 21
@@ -76,6 +81,8 @@ def load(path: str = LIB_PATH):
     lib.lcs_run.argtypes = [P, I64, P, I64, P, I, P, P]
     lib.lcs_status.argtypes = [P, P]
     lib.stencil_launch_count.argtypes = []
+    lib.stencil_checked_build.argtypes = []
+    lib.stencil_debug_check_index.argtypes = [I64, I64, P]
     lib.stencil_launch_count.restype = ctypes.c_uint64
     for name in EXPORTS:
         if name not in ("stencil_strerror", "stencil_launch_count"):
@@ -192,6 +199,16 @@ def stencil_debug_inject_stall(h, unit, spin=0):
 
 def stencil_launch_count() -> int:
     return int(load().stencil_launch_count())
+
+
+def checked_build() -> bool:
+    """True if the loaded library is the checked build."""
+    return bool(load().stencil_checked_build())
+
+
+def debug_check_index(i: int, n: int, stream=None) -> int:
+    """Run the checked build's index test of i against n in one device thread (no memory access)."""
+    return load().stencil_debug_check_index(int(i), int(n), _stream_ptr(stream))
 
 
 # ---- torch convenience ---------------------------------------------------------------------

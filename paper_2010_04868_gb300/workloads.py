@@ -43,9 +43,26 @@ import json
 
 from . import inputs
 
-# FP64 pipe of this GPU: 1.684 lane operations (DFMA, DMUL or DADD) per SM clock, 152 SMs
-FP64_OPS_PER_SM_CLK = 1.684
-N_SM = 152
+_PIPE = {}
+
+
+def pipe_peak_gops(sm_mhz):
+    """FP64 lane operations per second (in G) of this GPU at sm_mhz: the SM count read from the
+    device times the lane operations per SM clock that the FP64 pipe micro-benchmark
+    (peak/fp64_peak, built by build.build_probe) measures on it."""
+    if "ops" not in _PIPE:
+        import subprocess
+
+        import torch
+
+        from . import build as _b
+        out = subprocess.run([_b.build_probe()], capture_output=True, text=True, timeout=120).stdout
+        rows = [json.loads(ln) for ln in out.splitlines() if ln.startswith("{") and "fp64_lane_ops_per_sm_clk" in ln]
+        if not rows:
+            raise RuntimeError("FP64 probe printed no result: %s" % out[-300:])
+        _PIPE["ops"] = float(rows[-1]["fp64_lane_ops_per_sm_clk"])
+        _PIPE["nsm"] = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return _PIPE["ops"] * _PIPE["nsm"] * sm_mhz / 1e3
 
 CONFIGS = {
     # name: (dim, shape, method, ext, T, bc, weights seed offset or explicit weights)
@@ -140,7 +157,7 @@ def run(name, kernel="auto", T=None, reps=2, tb=0, tile=(0, 0, 0), sm_mhz=2070.0
     ms, launches = best
     gst = npts * T / ms / 1e6
     k = k_points(dim, shape, r)
-    peak = FP64_OPS_PER_SM_CLK * N_SM * sm_mhz / 1e3
+    peak = pipe_peak_gops(sm_mhz)
     # one pass per step moves the grid in and out, plus the K field planes with per-point weights
     bytes_pt = 16 + (8 * k if name in FIELD else 0)
     return {"config": name, "kernel": kernel, "r": r, "T": T, "ms": round(ms, 3), "gstencil_s": round(gst, 3),

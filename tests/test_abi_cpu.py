@@ -29,6 +29,19 @@ def test_library_exports_every_declared_symbol():
     assert declared == set(stencil.EXPORTS)
 
 
+def test_checked_build_exports_the_same_symbols_and_says_so():
+    """The checked build (every kernel index tested before its access) links from the same sources; the
+    query needs no GPU."""
+    import ctypes
+    from paper_2010_04868_gb300 import build, stencil
+    build.build()
+    chk = ctypes.CDLL(build.LIB_CHECKED)
+    missing = [n for n in sorted(_declared()) if not hasattr(chk, n)]
+    assert not missing, missing
+    assert chk.stencil_checked_build() == 1
+    assert stencil.load().stencil_checked_build() == 0
+
+
 def test_strerror_covers_codes():
     from paper_2010_04868_gb300 import stencil
     for code in range(0, -7, -1):
