@@ -114,9 +114,12 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
  *            constant boundary, tile[0] = CTAs per SM of the persistent
  *            kernel, in 2D tile[1] = skewed rows per tile (2..64) and, in 2D
  *            with radius 1, tile[2] = points per lane and step of the
- *            one-warp tile (8 or 16), or 1 for the decoupled tile of the
+ *            one-warp tile (8 or 16), 1 for the decoupled tile of the
  *            5-point star with one weight per term (a chain warp, producer
- *            warps and a scheduler warp per tile); for WAVEFRONT with a
+ *            warps and a scheduler warp per tile), or 2 for rows as lanes
+ *            (one weight per term: a warp's lanes hold 32 rows of one sweep,
+ *            the sweeps pipelined across warps; tile[0] = CTAs of four
+ *            warps per SM); for WAVEFRONT with a
  *            periodic boundary (the in-sweep tile DAG), tile[0] and tile[1] =
  *            lines per tile along axes 0 (3D) and 1, one thread each, at most
  *            256 in all, and tile[2] = hyperplane steps per tile; for STREAM,

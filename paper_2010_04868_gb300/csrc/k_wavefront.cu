@@ -810,6 +810,203 @@ __global__ void k_wave_prefix(WaveGeo wg, int64_t* pre)
     }
 }
 
+// ------------------------------------------------------- 2D: rows as lanes ---
+//
+// The same hyperplane order with the roles of the loops exchanged: the lanes
+// of a warp hold 32 consecutive rows of ONE sweep, and the sweeps are
+// pipelined across warps. Lane k updates column j = t - 2k of row 32b + k at
+// step t, so lane k - 1 finished the newest values above a point (columns
+// j - 1 .. j + 1) one to three steps before and hands them over by shuffle,
+// and lane k + 1 has not yet overwritten the old values below it (columns
+// j - 1 .. j + 1 of its own row, which it holds two to four steps ahead of
+// use) and hands those over too. A lane's only memory traffic is its own row:
+// one load (eight columns ahead) and one store per point. Lane 0 reads the
+// newest values of the row above the band from the band above, lane 31 the
+// old values of the row below it from the band below in the previous sweep.
+//
+// A task (s, b) is sweep s over band b. It waits (bounded) for the progress
+// words of (s, b - 1) (the row above, this sweep), (s - 1, b) (its own rows,
+// previous sweep) and (s - 1, b + 1) (the row below, previous sweep), once
+// per chunk of GR_CHUNK steps, for exactly the columns the chunk reads, and
+// publishes its own steps after each chunk. In-place updates are safe: a
+// value is overwritten only by a task that has waited for every reader of the
+// older value (the readers are the tasks it waits for, directly or through
+// them). Tasks are handed out in the order (s + b, s), in which every task a
+// task waits for comes earlier, so a persistent kernel whose warps claim
+// tasks from a ticket counter cannot deadlock. The sweeps need no blocking,
+// so no lane idles on a partial block of sweeps; the sum keeps the
+// descending order and rounding of every other kernel.
+constexpr int GR_CHUNK = 32;   // steps between progress waits and publications
+constexpr int GR_THREADS = 128;
+constexpr int GR_LAG = 62;     // steps lane 31 trails lane 0 (2 per lane)
+
+struct RowGeo {
+    int64_t n0, n1;   // rows, columns
+    int64_t nb;       // bands of 32 rows
+    int64_t T;        // sweeps of this launch
+    int64_t ntasks;   // T * nb
+    int64_t steps;    // steps of a task: n1 + GR_LAG, rounded up to GR_CHUNK
+};
+
+// The task of ticket tk in the order (s + b, s): (e, pe) is the caller's cursor (anti-diagonal e,
+// pe tickets before it); tickets only grow, so the cursor only moves forward.
+__device__ __forceinline__ void rows_decode(int64_t tk, const RowGeo& g, int64_t& e, int64_t& pe, int64_t& s,
+                                            int64_t& b)
+{
+    for (;;) {
+        const int64_t lo = e - g.nb + 1 > 0 ? e - g.nb + 1 : 0;
+        const int64_t hi = e < g.T - 1 ? e : g.T - 1;
+        const int64_t cnt = hi - lo + 1;
+        if (tk < pe + cnt) {
+            s = lo + (tk - pe);
+            b = e - s;
+            return;
+        }
+        pe += cnt;
+        ++e;
+    }
+}
+
+// Wait until *p >= need (lane 0); known caches the last value seen. False after a time-out.
+__device__ __forceinline__ bool rows_wait(const int* p, int need, int& known, int spin)
+{
+    if (known >= need) return true;
+    for (int it = 0; it < spin; ++it) {
+        known = ld_acquire(p);
+        if (known >= need) return true;
+        __nanosleep(it < 64 ? 64 : 512);
+    }
+    return false;
+}
+
+template <int SHAPE, int ARITH>
+__global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u, RowGeo g, double c,
+                                                          WArr<Stn<2, SHAPE, 1>::K> w, int* __restrict__ prog,
+                                                          int* __restrict__ ticket, int* status, WaitCfg wc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nprog = g.T * g.nb;
+    const int smax = (int)(g.n1 + GR_LAG);
+    int64_t e = 0, pe = 0;
+    bool timed_out = false;  // after a time-out this warp stops waiting (its results are void anyway)
+    for (;;) {
+        int64_t tk = 0;
+        if (lane == 0) tk = (int64_t)atomicAdd((unsigned long long*)ticket, 1ull);
+        tk = __shfl_sync(FULL, tk, 0);
+        if (tk >= g.ntasks) break;
+        int64_t s = 0, b = 0;
+        if (lane == 0) rows_decode(tk, g, e, pe, s, b);
+        s = __shfl_sync(FULL, s, 0);
+        b = __shfl_sync(FULL, b, 0);
+        const bool publish = tk != wc.stall;
+        const int64_t i = b * 32 + lane;
+        const bool row_ok = i < g.n0;
+        const double* row = u + (row_ok ? i : 0) * g.n1;
+        // lane 0: the row above the band (this sweep); lane 31: the row below it (previous sweep)
+        const int64_t ix = lane == 0 ? b * 32 - 1 : b * 32 + 32;
+        const bool x_ok = (lane == 0 || lane == 31) && ix >= 0 && ix < g.n0;
+        const double* xrow = u + (x_ok ? ix : 0) * g.n1;
+        const int64_t f = s * g.nb + b;
+        const int64_t fA = f - 1, fO = f - g.nb, fB = f - g.nb + 1;   // above / own / below predecessors
+        const bool hasA = b > 0, hasO = s > 0, hasB = s > 0 && b + 1 < g.nb;
+        int kA = 0, kO = 0, kB = 0;
+        // grid values written by other SMs: read through L2 (ld.global.cg), never from a stale L1 line
+        auto ld_row = [&](int64_t col) -> double {
+            return row_ok && col >= 0 && col < g.n1 && GBST_IN(col, g.n1) ? __ldcg(row + col) : c;
+        };
+        auto ld_x = [&](int64_t col) -> double {
+            return x_ok && col >= 0 && col < g.n1 && GBST_IN(col, g.n1) ? __ldcg(xrow + col) : c;
+        };
+        // RO[(m + q) & 7]: old value of this lane's row at column j + q (q = 0..7), j the column of step m;
+        // RX[(m + q) & 7]: lane 0 the newest row above, lane 31 the old row below, at j + q (q = -1..6);
+        // O[m & 3]: this lane's output of step m (c outside the grid)
+        double RO[8], RX[8], O[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) O[q] = c;
+        for (int64_t t0 = 0; t0 < g.steps; t0 += GR_CHUNK) {
+            if (lane == 0 && !timed_out) {
+                bool ok = true;
+                const int64_t nA = t0 + GR_CHUNK + 7 + GR_LAG, nO = t0 + GR_CHUNK + 8, nB = t0 + GR_CHUNK - 55;
+                if (hasA && GBST_IN(fA, nprog))
+                    ok &= rows_wait(prog + fA, (int)(nA < smax ? nA : smax), kA, wc.spin);
+                if (ok && hasO && GBST_IN(fO, nprog))
+                    ok &= rows_wait(prog + fO, (int)(nO < smax ? nO : smax), kO, wc.spin);
+                if (ok && hasB && nB > 0 && GBST_IN(fB, nprog))
+                    ok &= rows_wait(prog + fB, (int)(nB < smax ? nB : smax), kB, wc.spin);
+                if (!ok) {
+                    atomicExch(status, DEV_TIMEOUT);
+                    timed_out = true;
+                }
+            }
+            __syncwarp();
+            if (t0 == 0) {
+                const int64_t j0 = -2 * (int64_t)lane;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) RO[q] = ld_row(j0 + q);
+#pragma unroll
+                for (int q = -1; q < 7; ++q) RX[(q + 8) & 7] = ld_x(j0 + q);
+            }
+            for (int64_t tg = t0; tg < t0 + GR_CHUNK; tg += 8) {
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const int64_t j = tg + m - 2 * (int64_t)lane;
+                    double acc;
+                    if (SHAPE == STAR) {
+                        // (+1,0) (0,+1) (0,0) (0,-1) (-1,0)
+                        double bel = __shfl_down_sync(FULL, RO[(m + 2) & 7], 1);
+                        double abv = __shfl_up_sync(FULL, O[(m + 2) & 3], 1);
+                        if (lane == 31) bel = RX[m & 7];
+                        if (lane == 0) abv = RX[m & 7];
+                        acc = __dmul_rn(w.w[0], bel);
+                        acc = acc_step<ARITH>(acc, w.w[1], RO[(m + 1) & 7]);
+                        acc = acc_step<ARITH>(acc, w.w[2], RO[m & 7]);
+                        acc = acc_step<ARITH>(acc, w.w[3], O[(m + 3) & 3]);
+                        acc = acc_step<ARITH>(acc, w.w[4], abv);
+                    } else {
+                        // (+1,+1) (+1,0) (+1,-1) (0,+1) (0,0) (0,-1) (-1,+1) (-1,0) (-1,-1)
+                        double br = __shfl_down_sync(FULL, RO[(m + 3) & 7], 1);
+                        double bc = __shfl_down_sync(FULL, RO[(m + 2) & 7], 1);
+                        double bl = __shfl_down_sync(FULL, RO[(m + 1) & 7], 1);
+                        double ar = __shfl_up_sync(FULL, O[(m + 3) & 3], 1);
+                        double ac = __shfl_up_sync(FULL, O[(m + 2) & 3], 1);
+                        double al = __shfl_up_sync(FULL, O[(m + 1) & 3], 1);
+                        if (lane == 31) {
+                            br = RX[(m + 1) & 7];
+                            bc = RX[m & 7];
+                            bl = RX[(m + 7) & 7];
+                        }
+                        if (lane == 0) {
+                            ar = RX[(m + 1) & 7];
+                            ac = RX[m & 7];
+                            al = RX[(m + 7) & 7];
+                        }
+                        acc = __dmul_rn(w.w[0], br);
+                        acc = acc_step<ARITH>(acc, w.w[1], bc);
+                        acc = acc_step<ARITH>(acc, w.w[2], bl);
+                        acc = acc_step<ARITH>(acc, w.w[3], RO[(m + 1) & 7]);
+                        acc = acc_step<ARITH>(acc, w.w[4], RO[m & 7]);
+                        acc = acc_step<ARITH>(acc, w.w[5], O[(m + 3) & 3]);
+                        acc = acc_step<ARITH>(acc, w.w[6], ar);
+                        acc = acc_step<ARITH>(acc, w.w[7], ac);
+                        acc = acc_step<ARITH>(acc, w.w[8], al);
+                    }
+                    const bool jin = j >= 0 && j < g.n1;
+                    const double out = jin ? acc : c;
+                    O[m & 3] = out;
+                    if (jin && row_ok && GBST_IN(j, g.n1)) __stcg(u + i * g.n1 + j, out);
+                    RO[m & 7] = ld_row(j + 8);
+                    RX[(m + 7) & 7] = ld_x(j + 7);
+                }
+            }
+            __syncwarp();
+            if (lane == 0 && publish && GBST_IN(f, nprog)) {
+                __threadfence();
+                st_release(prog + f, (int)(t0 + GR_CHUNK));
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------- periodic: in-sweep DAG ---
 //
 // With a periodic boundary, sweep t+1 reads (through the wrap) values sweep t
@@ -1285,6 +1482,56 @@ static int launch_sweepdag(const RunCtx& ctx, double* u, const WS& w, const Swee
     return cuda_rc(cudaGetLastError());
 }
 
+// 2D Gauss-Seidel, rows as lanes (k_gs2d_rows): constant boundary, radius 1, constant weights.
+// Sweeps go to launches of at most GR_MAX_TASKS tasks (progress words) each.
+constexpr int64_t GR_MAX_TASKS = (int64_t)1 << 24;
+
+template <int SHAPE>
+static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
+{
+    stencil_handle_s* h = ctx.h;
+    RowGeo g;
+    g.n0 = ctx.g.n1;
+    g.n1 = ctx.g.n2;
+    g.nb = (g.n0 + 31) / 32;
+    g.steps = (g.n1 + GR_LAG + GR_CHUNK - 1) / GR_CHUNK * GR_CHUNK;
+    if (g.n1 + GR_LAG + GR_CHUNK > INT32_MAX) return STENCIL_EUNSUPPORTED;  // progress words are int
+    const int64_t tmax = GR_MAX_TASKS / g.nb > 0 ? GR_MAX_TASKS / g.nb : 1;
+    const int64_t tl = T < tmax ? T : tmax;  // sweeps per launch
+    const size_t bytes = 256 + (size_t)(tl * g.nb) * sizeof(int);
+    int rc = wave_workspace(h, bytes, ctx.st);
+    if (rc || prepare_only) return rc;
+    int* ticket = (int*)h->wave_ws;
+    int* prog = (int*)((char*)h->wave_ws + 256);
+    constexpr int K = Stn<2, SHAPE, 1>::K;
+    WArr<K> w;
+    for (int q = 0; q < K; ++q) w.w[q] = h->w_desc[q];
+    auto kern = h->arith == ARITH_FMA ? k_gs2d_rows<SHAPE, ARITH_FMA> : k_gs2d_rows<SHAPE, ARITH_UNFUSED>;
+    int nsm = 0, per_sm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GR_THREADS, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return STENCIL_ECUDA;
+    }
+    // CTAs of four worker warps per SM: 4 by default, or what the wavefront plan asks for (tile[0])
+    const int want = ctx.wtile[0] > 0 ? (int)ctx.wtile[0] : 4;
+    const WaitCfg wc = take_wait_cfg(h);
+    for (int64_t s0 = 0; s0 < T; s0 += tl) {
+        g.T = T - s0 < tl ? T - s0 : tl;
+        g.ntasks = g.T * g.nb;
+        int64_t nblk = (int64_t)nsm * (per_sm < want ? per_sm : want);
+        const int64_t need = (g.ntasks + GR_THREADS / 32 - 1) / (GR_THREADS / 32);
+        if (nblk > need) nblk = need;
+        if (cudaMemsetAsync(ticket, 0, 8, ctx.st) != cudaSuccess) return STENCIL_ECUDA;
+        if (cudaMemsetAsync(prog, 0, (size_t)g.ntasks * sizeof(int), ctx.st) != cudaSuccess) return STENCIL_ECUDA;
+        kern<<<(unsigned)nblk, GR_THREADS, 0, ctx.st>>>(u, g, h->c, w, prog, ticket, h->d_status, wc);
+        g_launches++;
+        if (cudaGetLastError() != cudaSuccess) return STENCIL_ECUDA;
+    }
+    return STENCIL_OK;
+}
+
 static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, bool prep)
 {
     const stencil_handle_s* h = ctx.h;
@@ -1310,6 +1557,9 @@ static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, boo
         // (measured level with the one-warp tile at best, so not the default)
         const int64_t pw = ctx.wtile[2];
         const bool w8 = pw == 8;
+        // tile[2] = 2: rows as lanes (radius 1, constant weights)
+        if (pw == 2 && h->r == 1 && !ctx.sd.field)
+            return h->shape == STAR ? gs2d_rows<STAR>(ctx, u, T, prep) : gs2d_rows<BOX>(ctx, u, T, prep);
         if (h->shape == STAR && h->r == 1)
             return w8 ? wave_tiles<2, STAR, 1, 8>(ctx, u, T, lanes, prep)
                       : wave_tiles<2, STAR, 1, 16>(ctx, u, T, lanes, prep, pw == 1 && !ctx.sd.field);

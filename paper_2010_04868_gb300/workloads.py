@@ -233,8 +233,9 @@ def run_lcs(kernel="bits", n=200000, sigma=4, reps=2):
             "gcell_updates_s": round(n * n / ms / 1e6, 1), "launches": launches, "lcs_length": int(row[-1])}
 
 
-def run_batch3d(reps=2):
-    """The three 512^3 periodic problems batched, and the same three run separately."""
+def run_batch3d(reps=2, ext=None, T=None):
+    """The three 512^3 periodic problems batched, and the same three run separately (ext and T
+    override the extents and the steps per problem: a smaller case of the same batch)."""
     import ctypes
 
     import torch
@@ -243,14 +244,15 @@ def run_batch3d(reps=2):
     names = ["jacobi3d7", "jacobi3d27", "gs3d7"]
     sts, us, scs, u0s = [], [], [], []
     for n in names:
-        dim, shape, method, ext, T, bc, _ = CONFIGS[n]
-        u0 = torch.from_numpy(config_grid(n)).cuda()
+        dim, shape, method, ext0, _, bc, _ = CONFIGS[n]
+        e = tuple(ext) if ext else ext0
+        u0 = torch.from_numpy(config_grid(n) if e == ext0 else inputs.grid(inputs.SEED_BASE + 10, e)).cuda()
         st = S.Stencil(dim, shape, 1, config_weights(n), method, bc)
         sts.append(st)
         u0s.append(u0)
         us.append(u0.clone())
         scs.append(torch.empty_like(u0) if method == 0 else None)
-    Ts = [CONFIGS[n][4] for n in names]
+    Ts = [CONFIGS[n][4] if T is None else T for n in names]
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     grids = [st.grid(u, sc) for st, u, sc in zip(sts, us, scs)]
 
@@ -276,8 +278,11 @@ def run_batch3d(reps=2):
         if st.status() != 0:
             raise RuntimeError("batch3d: device status")
         st.close()
-    upd = sum(512 ** 3 * T for T in Ts)
-    return {"config": "batch3d", "ms_batch": round(ms_batch, 2), "ms_separate": round(ms_solo, 2),
+    npts = 1
+    for e in us[0].shape:
+        npts *= e
+    upd = sum(npts * t for t in Ts)
+    return {"config": "batch3d", "ext": list(us[0].shape), "T": Ts, "ms_batch": round(ms_batch, 2), "ms_separate": round(ms_solo, 2),
             "gstencil_s_batch": round(upd / ms_batch / 1e6, 3), "gstencil_s_separate": round(upd / ms_solo / 1e6, 3)}
 
 
@@ -295,7 +300,8 @@ def main():
     tile = tuple(int(x) for x in a.tile.split(","))
     for n in names:
         if n == "batch3d":
-            print(json.dumps(run_batch3d(a.reps)), flush=True)
+            ext = tuple(int(x) for x in a.ext.split(",")) if a.ext else None
+            print(json.dumps(run_batch3d(a.reps, ext=ext, T=a.T)), flush=True)
         elif n == "life":
             print(json.dumps(run_life(a.T or 2000, a.tb, a.reps)), flush=True)
         elif n == "lcs":

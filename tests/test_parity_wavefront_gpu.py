@@ -164,3 +164,70 @@ def test_periodic_sweep_dag_tile_shapes(dim, r, ext, tile):
     ref = oracle_run(u0, 5, dim, "star", r, w, "gs", "periodic", 0.0, "fma")
     got = gpu_run(u0, 5, dim, "star", r, w, "gs", "periodic", 0.0, "fma", plan=WAVE, tile=tile)
     assert bits_equal(got, ref), first_diff(got, ref)
+
+
+ROWS = (0, 0, 2)   # wavefront plan: rows as lanes
+
+
+@pytest.mark.parametrize("shape,ext", [("star", (1, 1)), ("star", (1, 70)), ("star", (70, 1)), ("star", (32, 64)),
+                                       ("star", (33, 65)), ("star", (130, 77)), ("star", (31, 200)),
+                                       ("box", (1, 1)), ("box", (2, 3)), ("box", (64, 31)), ("box", (70, 131)),
+                                       ("box", (97, 33))])
+@pytest.mark.parametrize("c", [0.0, 0.3])
+def test_gs2d_rows_equals_oracle(shape, ext, c):
+    """Rows as lanes (tile[2] = 2): ragged bands and rows shorter than the lanes' skew, both rounding modes."""
+    w, u0 = case(2, shape, 1, ext, seed=ext[0] + 3 * ext[1])
+    for T in (1, 2, 5, 33):
+        for arith in ("fma", "unfused"):
+            ref = oracle_run(u0, T, 2, shape, 1, w, "gs", "constant", c, arith)
+            got = gpu_run(u0, T, 2, shape, 1, w, "gs", "constant", c, arith, plan=WAVE, tile=ROWS)
+            assert bits_equal(got, ref), (T, arith, first_diff(got, ref))
+
+
+@pytest.mark.parametrize("ctas", [1, 2, 6])
+def test_gs2d_rows_ctas_per_sm(ctas):
+    """The CTAs per SM a plan asks for (tile[0]) change nothing in the result."""
+    w, u0 = case(2, "star", 1, (300, 257), seed=5)
+    ref = oracle_run(u0, 40, 2, "star", 1, w, "gs", "constant", 0.1, "fma")
+    got = gpu_run(u0, 40, 2, "star", 1, w, "gs", "constant", 0.1, "fma", plan=WAVE, tile=(ctas, 0, 2))
+    assert bits_equal(got, ref), first_diff(got, ref)
+
+
+@pytest.mark.parametrize("shape", ["star", "box"])
+def test_gs2d_rows_full_size_equals_oracle(shape):
+    """The 4096^2 Gauss-Seidel workload's grid with rows as lanes, T cut to 24 for the serial oracle."""
+    from paper_2010_04868_gb300 import inputs
+    u0 = inputs.grid(inputs.SEED_BASE + 3, (4096, 4096))
+    w = inputs.normalized_weights(inputs.SEED_BASE + 105, 5 if shape == "star" else 9)
+    ref = oracle_run(u0, 24, 2, shape, 1, w, "gs", "constant", 0.0, "fma")
+    got = gpu_run(u0, 24, 2, shape, 1, w, "gs", "constant", 0.0, "fma", plan=WAVE, tile=ROWS)
+    assert bits_equal(got, ref), first_diff(got, ref)
+
+
+def test_gs2d_rows_full_size_full_T_equals_plain():
+    """Full 4096^2 x 200 sweeps: rows as lanes and the plain sweep kernel agree bit for bit."""
+    from paper_2010_04868_gb300 import inputs
+    u0 = inputs.grid(inputs.SEED_BASE + 3, (4096, 4096))
+    w = inputs.normalized_weights(inputs.SEED_BASE + 105, 5)
+    a = gpu_run(u0, 200, 2, "star", 1, w, "gs", "constant", 0.0, "fma", plan=WAVE, tile=ROWS)
+    b = gpu_run(u0, 200, 2, "star", 1, w, "gs", "constant", 0.0, "fma", plan=PLAIN)
+    assert bits_equal(a, b), first_diff(a, b)
+
+
+def test_gs2d_rows_stalled_task_times_out_without_hanging():
+    """A task that never publishes its progress: the tasks waiting on it give up (bounded), the run
+    reports STENCIL_ETIMEOUT, and the next run on the same handle is correct."""
+    import torch
+    from paper_2010_04868_gb300 import stencil as S
+    w, u0 = case(2, "star", 1, (100, 90), seed=8)
+    st = S.Stencil(2, 0, 1, list(w), S.STENCIL_GAUSS_SEIDEL, S.STENCIL_BC_CONSTANT, 0.0).set_plan(WAVE, 0, ROWS)
+    u = torch.from_numpy(u0.copy()).cuda()
+    S.stencil_debug_inject_stall(st.handle, 3, 20000)
+    st.run(u, 6)
+    assert st.status() == S.STENCIL_ETIMEOUT
+    u.copy_(torch.from_numpy(u0))
+    st.run(u, 6)
+    assert st.status() == S.STENCIL_OK
+    ref = oracle_run(u0, 6, 2, "star", 1, w, "gs", "constant", 0.0, "fma")
+    assert bits_equal(u.cpu().numpy(), ref)
+    st.close()
