@@ -887,6 +887,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
     const int lane = threadIdx.x & 31;
     const int64_t nprog = g.T * g.nb;
     const int smax = (int)(g.n1 + GR_LAG);
+    const int n1 = (int)g.n1, steps = (int)g.steps;  // columns and steps fit in int (checked by the host)
     int64_t e = 0, pe = 0;
     bool timed_out = false;  // after a time-out this warp stops waiting (its results are void anyway)
     for (;;) {
@@ -901,7 +902,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
         const bool publish = tk != wc.stall;
         const int64_t i = b * 32 + lane;
         const bool row_ok = i < g.n0;
-        const double* row = u + (row_ok ? i : 0) * g.n1;
+        double* const row = u + (row_ok ? i : 0) * g.n1;
         // lane 0: the row above the band (this sweep); lane 31: the row below it (previous sweep)
         const int64_t ix = lane == 0 ? b * 32 - 1 : b * 32 + 32;
         const bool x_ok = (lane == 0 || lane == 31) && ix >= 0 && ix < g.n0;
@@ -911,11 +912,11 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
         const bool hasA = b > 0, hasO = s > 0, hasB = s > 0 && b + 1 < g.nb;
         int kA = 0, kO = 0, kB = 0;
         // grid values written by other SMs: read through L2 (ld.global.cg), never from a stale L1 line
-        auto ld_row = [&](int64_t col) -> double {
-            return row_ok && col >= 0 && col < g.n1 && GBST_IN(col, g.n1) ? __ldcg(row + col) : c;
+        auto ld_row = [&](int col) -> double {
+            return row_ok && col >= 0 && col < n1 && GBST_IN(col, n1) ? __ldcg(row + col) : c;
         };
-        auto ld_x = [&](int64_t col) -> double {
-            return x_ok && col >= 0 && col < g.n1 && GBST_IN(col, g.n1) ? __ldcg(xrow + col) : c;
+        auto ld_x = [&](int col) -> double {
+            return x_ok && col >= 0 && col < n1 && GBST_IN(col, n1) ? __ldcg(xrow + col) : c;
         };
         // RO[(m + q) & 7]: old value of this lane's row at column j + q (q = 0..7), j the column of step m;
         // RX[(m + q) & 7]: lane 0 the newest row above, lane 31 the old row below, at j + q (q = -1..6);
@@ -923,16 +924,16 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
         double RO[8], RX[8], O[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) O[q] = c;
-        for (int64_t t0 = 0; t0 < g.steps; t0 += GR_CHUNK) {
+        for (int t0 = 0; t0 < steps; t0 += GR_CHUNK) {
             if (lane == 0 && !timed_out) {
                 bool ok = true;
-                const int64_t nA = t0 + GR_CHUNK + 7 + GR_LAG, nO = t0 + GR_CHUNK + 8, nB = t0 + GR_CHUNK - 55;
+                const int nA = t0 + GR_CHUNK + 7 + GR_LAG, nO = t0 + GR_CHUNK + 8, nB = t0 + GR_CHUNK - 55;
                 if (hasA && GBST_IN(fA, nprog))
-                    ok &= rows_wait(prog + fA, (int)(nA < smax ? nA : smax), kA, wc.spin);
+                    ok &= rows_wait(prog + fA, nA < smax ? nA : smax, kA, wc.spin);
                 if (ok && hasO && GBST_IN(fO, nprog))
-                    ok &= rows_wait(prog + fO, (int)(nO < smax ? nO : smax), kO, wc.spin);
+                    ok &= rows_wait(prog + fO, nO < smax ? nO : smax, kO, wc.spin);
                 if (ok && hasB && nB > 0 && GBST_IN(fB, nprog))
-                    ok &= rows_wait(prog + fB, (int)(nB < smax ? nB : smax), kB, wc.spin);
+                    ok &= rows_wait(prog + fB, nB < smax ? nB : smax, kB, wc.spin);
                 if (!ok) {
                     atomicExch(status, DEV_TIMEOUT);
                     timed_out = true;
@@ -940,16 +941,16 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
             }
             __syncwarp();
             if (t0 == 0) {
-                const int64_t j0 = -2 * (int64_t)lane;
+                const int j0 = -2 * lane;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) RO[q] = ld_row(j0 + q);
 #pragma unroll
                 for (int q = -1; q < 7; ++q) RX[(q + 8) & 7] = ld_x(j0 + q);
             }
-            for (int64_t tg = t0; tg < t0 + GR_CHUNK; tg += 8) {
+            for (int tg = t0; tg < t0 + GR_CHUNK; tg += 8) {
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
-                    const int64_t j = tg + m - 2 * (int64_t)lane;
+                    const int j = tg + m - 2 * lane;
                     double acc;
                     if (SHAPE == STAR) {
                         // (+1,0) (0,+1) (0,0) (0,-1) (-1,0)
@@ -990,10 +991,10 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
                         acc = acc_step<ARITH>(acc, w.w[7], ac);
                         acc = acc_step<ARITH>(acc, w.w[8], al);
                     }
-                    const bool jin = j >= 0 && j < g.n1;
+                    const bool jin = j >= 0 && j < n1;
                     const double out = jin ? acc : c;
                     O[m & 3] = out;
-                    if (jin && row_ok && GBST_IN(j, g.n1)) __stcg(u + i * g.n1 + j, out);
+                    if (jin && row_ok && GBST_IN(j, n1)) __stcg(row + j, out);
                     RO[m & 7] = ld_row(j + 8);
                     RX[(m + 7) & 7] = ld_x(j + 7);
                 }
@@ -1001,7 +1002,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
             __syncwarp();
             if (lane == 0 && publish && GBST_IN(f, nprog)) {
                 __threadfence();
-                st_release(prog + f, (int)(t0 + GR_CHUNK));
+                st_release(prog + f, t0 + GR_CHUNK);
             }
         }
     }
