@@ -827,7 +827,7 @@ __global__ void k_wave_prefix(WaveGeo wg, int64_t* pre)
 // A task (s, b) is sweep s over band b. It waits (bounded) for the progress
 // words of (s, b - 1) (the row above, this sweep), (s - 1, b) (its own rows,
 // previous sweep) and (s - 1, b + 1) (the row below, previous sweep), once
-// per chunk of GR_CHUNK steps, for exactly the columns the chunk reads, and
+// per chunk of CH steps, for exactly the columns the chunk reads, and
 // publishes its own steps after each chunk. In-place updates are safe: a
 // value is overwritten only by a task that has waited for every reader of the
 // older value (the readers are the tasks it waits for, directly or through
@@ -836,7 +836,7 @@ __global__ void k_wave_prefix(WaveGeo wg, int64_t* pre)
 // tasks from a ticket counter cannot deadlock. The sweeps need no blocking,
 // so no lane idles on a partial block of sweeps; the sum keeps the
 // descending order and rounding of every other kernel.
-constexpr int GR_CHUNK = 32;   // steps between progress waits and publications
+constexpr int GR_CHUNK = 32;   // default steps between progress waits and publications (CH)
 constexpr int GR_THREADS = 128;
 constexpr int GR_LAG = 62;     // steps lane 31 trails lane 0 (2 per lane)
 
@@ -845,7 +845,7 @@ struct RowGeo {
     int64_t nb;       // bands of 32 rows
     int64_t T;        // sweeps of this launch
     int64_t ntasks;   // T * nb
-    int64_t steps;    // steps of a task: n1 + GR_LAG, rounded up to GR_CHUNK
+    int64_t steps;    // steps of a task: n1 + GR_LAG, rounded up to the chunk
 };
 
 // The task of ticket tk in the order (s + b, s): (e, pe) is the caller's cursor (anti-diagonal e,
@@ -867,6 +867,26 @@ __device__ __forceinline__ void rows_decode(int64_t tk, const RowGeo& g, int64_t
     }
 }
 
+// Predicated global accesses through L2 without a branch: a lane whose predicate is false touches no
+// memory and (load) keeps the default in its register.
+__device__ __forceinline__ double ldcg_if(const double* p, bool pred, double dflt)
+{
+    double v = dflt;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.cg.f64 %0, [%1];\n\t}"
+        : "+d"(v)
+        : "l"(p), "r"((unsigned)pred)
+        : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void stcg_if(double* p, bool pred, double v)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.cg.f64 [%0], %1;\n\t}" ::"l"(p),
+                 "d"(v), "r"((unsigned)pred)
+                 : "memory");
+}
+
 // Wait until *p >= need (lane 0); known caches the last value seen. False after a time-out.
 __device__ __forceinline__ bool rows_wait(const int* p, int need, int& known, int spin)
 {
@@ -879,7 +899,7 @@ __device__ __forceinline__ bool rows_wait(const int* p, int need, int& known, in
     return false;
 }
 
-template <int SHAPE, int ARITH>
+template <int SHAPE, int ARITH, int CH>
 __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u, RowGeo g, double c,
                                                           WArr<Stn<2, SHAPE, 1>::K> w, int* __restrict__ prog,
                                                           int* __restrict__ ticket, int* status, WaitCfg wc)
@@ -911,12 +931,13 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
         const int64_t fA = f - 1, fO = f - g.nb, fB = f - g.nb + 1;   // above / own / below predecessors
         const bool hasA = b > 0, hasO = s > 0, hasB = s > 0 && b + 1 < g.nb;
         int kA = 0, kO = 0, kB = 0;
-        // grid values written by other SMs: read through L2 (ld.global.cg), never from a stale L1 line
+        // grid values written by other SMs: read through L2 (ld.global.cg), never from a stale L1 line;
+        // the predicates keep every access inside the grid (c stands for a value outside it)
         auto ld_row = [&](int col) -> double {
-            return row_ok && col >= 0 && col < n1 && GBST_IN(col, n1) ? __ldcg(row + col) : c;
+            return ldcg_if(row + col, row_ok && (unsigned)col < (unsigned)n1 && GBST_IN(col, n1), c);
         };
         auto ld_x = [&](int col) -> double {
-            return x_ok && col >= 0 && col < n1 && GBST_IN(col, n1) ? __ldcg(xrow + col) : c;
+            return ldcg_if(xrow + col, x_ok && (unsigned)col < (unsigned)n1 && GBST_IN(col, n1), c);
         };
         // RO[(m + q) & 7]: old value of this lane's row at column j + q (q = 0..7), j the column of step m;
         // RX[(m + q) & 7]: lane 0 the newest row above, lane 31 the old row below, at j + q (q = -1..6);
@@ -924,10 +945,10 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
         double RO[8], RX[8], O[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) O[q] = c;
-        for (int t0 = 0; t0 < steps; t0 += GR_CHUNK) {
+        for (int t0 = 0; t0 < steps; t0 += CH) {
             if (lane == 0 && !timed_out) {
                 bool ok = true;
-                const int nA = t0 + GR_CHUNK + 7 + GR_LAG, nO = t0 + GR_CHUNK + 8, nB = t0 + GR_CHUNK - 55;
+                const int nA = t0 + CH + 7 + GR_LAG, nO = t0 + CH + 8, nB = t0 + CH - 55;
                 if (hasA && GBST_IN(fA, nprog))
                     ok &= rows_wait(prog + fA, nA < smax ? nA : smax, kA, wc.spin);
                 if (ok && hasO && GBST_IN(fO, nprog))
@@ -947,7 +968,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
 #pragma unroll
                 for (int q = -1; q < 7; ++q) RX[(q + 8) & 7] = ld_x(j0 + q);
             }
-            for (int tg = t0; tg < t0 + GR_CHUNK; tg += 8) {
+            for (int tg = t0; tg < t0 + CH; tg += 8) {
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
                     const int j = tg + m - 2 * lane;
@@ -991,10 +1012,10 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
                         acc = acc_step<ARITH>(acc, w.w[7], ac);
                         acc = acc_step<ARITH>(acc, w.w[8], al);
                     }
-                    const bool jin = j >= 0 && j < n1;
+                    const bool jin = (unsigned)j < (unsigned)n1;
                     const double out = jin ? acc : c;
                     O[m & 3] = out;
-                    if (jin && row_ok && GBST_IN(j, n1)) __stcg(row + j, out);
+                    stcg_if(row + j, jin && row_ok && GBST_IN(j, n1), out);
                     RO[m & 7] = ld_row(j + 8);
                     RX[(m + 7) & 7] = ld_x(j + 7);
                 }
@@ -1002,7 +1023,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
             __syncwarp();
             if (lane == 0 && publish && GBST_IN(f, nprog)) {
                 __threadfence();
-                st_release(prog + f, t0 + GR_CHUNK);
+                st_release(prog + f, t0 + CH);
             }
         }
     }
@@ -1487,7 +1508,7 @@ static int launch_sweepdag(const RunCtx& ctx, double* u, const WS& w, const Swee
 // Sweeps go to launches of at most GR_MAX_TASKS tasks (progress words) each.
 constexpr int64_t GR_MAX_TASKS = (int64_t)1 << 24;
 
-template <int SHAPE>
+template <int SHAPE, int CH>
 static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
 {
     stencil_handle_s* h = ctx.h;
@@ -1495,8 +1516,8 @@ static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
     g.n0 = ctx.g.n1;
     g.n1 = ctx.g.n2;
     g.nb = (g.n0 + 31) / 32;
-    g.steps = (g.n1 + GR_LAG + GR_CHUNK - 1) / GR_CHUNK * GR_CHUNK;
-    if (g.n1 + GR_LAG + GR_CHUNK > INT32_MAX) return STENCIL_EUNSUPPORTED;  // progress words are int
+    g.steps = (g.n1 + GR_LAG + CH - 1) / CH * CH;
+    if (g.n1 + GR_LAG + CH > INT32_MAX) return STENCIL_EUNSUPPORTED;  // progress words are int
     const int64_t tmax = GR_MAX_TASKS / g.nb > 0 ? GR_MAX_TASKS / g.nb : 1;
     const int64_t tl = T < tmax ? T : tmax;  // sweeps per launch
     const size_t bytes = 256 + (size_t)(tl * g.nb) * sizeof(int);
@@ -1507,7 +1528,7 @@ static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
     constexpr int K = Stn<2, SHAPE, 1>::K;
     WArr<K> w;
     for (int q = 0; q < K; ++q) w.w[q] = h->w_desc[q];
-    auto kern = h->arith == ARITH_FMA ? k_gs2d_rows<SHAPE, ARITH_FMA> : k_gs2d_rows<SHAPE, ARITH_UNFUSED>;
+    auto kern = h->arith == ARITH_FMA ? k_gs2d_rows<SHAPE, ARITH_FMA, CH> : k_gs2d_rows<SHAPE, ARITH_UNFUSED, CH>;
     int nsm = 0, per_sm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1531,6 +1552,15 @@ static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
         if (cudaGetLastError() != cudaSuccess) return STENCIL_ECUDA;
     }
     return STENCIL_OK;
+}
+
+// steps per chunk of the rows pipeline: 32, or 64 / 128 when the wavefront plan asks (tile[1])
+template <int SHAPE>
+static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
+{
+    if (ctx.wtile[1] == 64) return gs2d_rows<SHAPE, 64>(ctx, u, T, prepare_only);
+    if (ctx.wtile[1] == 128) return gs2d_rows<SHAPE, 128>(ctx, u, T, prepare_only);
+    return gs2d_rows<SHAPE, GR_CHUNK>(ctx, u, T, prepare_only);
 }
 
 static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, bool prep)

@@ -184,12 +184,14 @@ def test_gs2d_rows_equals_oracle(shape, ext, c):
             assert bits_equal(got, ref), (T, arith, first_diff(got, ref))
 
 
-@pytest.mark.parametrize("ctas", [1, 2, 6])
-def test_gs2d_rows_ctas_per_sm(ctas):
-    """The CTAs per SM a plan asks for (tile[0]) change nothing in the result."""
-    w, u0 = case(2, "star", 1, (300, 257), seed=5)
-    ref = oracle_run(u0, 40, 2, "star", 1, w, "gs", "constant", 0.1, "fma")
-    got = gpu_run(u0, 40, 2, "star", 1, w, "gs", "constant", 0.1, "fma", plan=WAVE, tile=(ctas, 0, 2))
+@pytest.mark.parametrize("shape", ["star", "box"])
+@pytest.mark.parametrize("tile", [(1, 0, 2), (2, 0, 2), (6, 0, 2), (4, 64, 2), (3, 128, 2), (1, 128, 2)])
+def test_gs2d_rows_plan_parameters(shape, tile):
+    """The CTAs per SM (tile[0]) and the steps per chunk (tile[1]: 64 or 128) a plan asks for change
+    nothing in the result."""
+    w, u0 = case(2, shape, 1, (300, 257), seed=5)
+    ref = oracle_run(u0, 40, 2, shape, 1, w, "gs", "constant", 0.1, "fma")
+    got = gpu_run(u0, 40, 2, shape, 1, w, "gs", "constant", 0.1, "fma", plan=WAVE, tile=tile)
     assert bits_equal(got, ref), first_diff(got, ref)
 
 

@@ -1,8 +1,8 @@
 """CPU restatement of the rows-as-lanes 2D Gauss-Seidel pipeline (k_gs2d_rows in csrc/k_wavefront.cu).
 
 A task (s, b) is sweep s over band b (32 rows, one per lane); lane k updates column t - 2k at step t.
-Each chunk of 32 steps first waits for the progress of (s, b-1), (s-1, b) and (s-1, b+1), then runs,
-then publishes. Every load a chunk issues (a lane's own row eight columns ahead, lane 0's row above and
+Each chunk of ch steps (32 by default, 64 or 128 when a plan asks) first waits for the progress of
+(s, b-1), (s-1, b) and (s-1, b+1), then runs, then publishes. Every load a chunk issues (a lane's own row eight columns ahead, lane 0's row above and
 lane 31's row below seven columns ahead, and the first chunk's ring fill) and every store is placed in
 the chunk that issues it. The checks, on small ragged grids:
   * every wait names a task with an earlier ticket (tickets in the order (s + b, s)), so the
@@ -20,21 +20,21 @@ import pytest
 from helpers import case, oracle_run
 from paper_2010_04868_gb300 import inputs
 
-CHUNK, LAG = 32, 62
+LAG = 62
 
 
-def geometry(n0, n1, T):
+def geometry(n0, n1, T, ch):
     nb = -(-n0 // 32)
-    steps = -(-(n1 + LAG) // CHUNK) * CHUNK
+    steps = -(-(n1 + LAG) // ch) * ch
     order = [(s, e - s) for e in range(T + nb - 1) for s in range(max(0, e - nb + 1), min(T - 1, e) + 1)]
     return nb, steps, order
 
 
-def chunk_waits(s, b, t0, nb, n1):
+def chunk_waits(s, b, t0, nb, n1, ch):
     """(task, progress needed) pairs a chunk starting at step t0 waits for (the kernel's nA, nO, nB)."""
     smax = n1 + LAG
     out = []
-    nA, nO, nB = t0 + CHUNK + 7 + LAG, t0 + CHUNK + 8, t0 + CHUNK - 55
+    nA, nO, nB = t0 + ch + 7 + LAG, t0 + ch + 8, t0 + ch - 55
     if b > 0:
         out.append(((s, b - 1), min(nA, smax)))
     if s > 0:
@@ -44,14 +44,14 @@ def chunk_waits(s, b, t0, nb, n1):
     return out
 
 
-def chunk_access(s, b, c, n0, n1):
+def chunk_access(s, b, c, n0, n1, ch):
     """Points a chunk reads and writes."""
     rd, wr = set(), set()
 
     def add(row, col, into):
         if 0 <= row < n0 and 0 <= col < n1:
             into.add((row, col))
-    t0 = c * CHUNK
+    t0 = c * ch
     if c == 0:
         for k in range(32):
             for q in range(8):
@@ -59,7 +59,7 @@ def chunk_access(s, b, c, n0, n1):
         for q in range(-1, 7):
             add(32 * b - 1, q, rd)
             add(32 * b + 32, -LAG + q, rd)
-    for t in range(t0, t0 + CHUNK):
+    for t in range(t0, t0 + ch):
         for k in range(32):
             j = t - 2 * k
             add(32 * b + k, j, wr)
@@ -72,11 +72,12 @@ def chunk_access(s, b, c, n0, n1):
 CASES = [(40, 37, 3), (64, 50, 3), (33, 70, 3), (5, 9, 4), (70, 13, 3), (70, 150, 3), (96, 40, 2), (1, 1, 2)]
 
 
+@pytest.mark.parametrize("ch", [32, 64])
 @pytest.mark.parametrize("n0,n1,T", CASES)
-def test_waits_point_back_and_unordered_chunks_do_not_conflict(n0, n1, T):
-    nb, steps, order = geometry(n0, n1, T)
+def test_waits_point_back_and_unordered_chunks_do_not_conflict(n0, n1, T, ch):
+    nb, steps, order = geometry(n0, n1, T, ch)
     ticket = {x: q for q, x in enumerate(order)}
-    nch = steps // CHUNK
+    nch = steps // ch
     inst = [(x, c) for x in order for c in range(nch)]
     idx = {v: q for q, v in enumerate(inst)}
     pred = [0] * len(inst)
@@ -85,13 +86,13 @@ def test_waits_point_back_and_unordered_chunks_do_not_conflict(n0, n1, T):
         p = 0
         if c > 0:
             p |= pred[idx[((s, b), c - 1)]] | (1 << idx[((s, b), c - 1)])
-        for (y, need) in chunk_waits(s, b, c * CHUNK, nb, n1):
+        for (y, need) in chunk_waits(s, b, c * ch, nb, n1, ch):
             assert ticket[y] < ticket[(s, b)], "a wait names a later ticket"
-            cy = -(-need // CHUNK) - 1          # the chunk whose publication first reaches need
+            cy = -(-need // ch) - 1          # the chunk whose publication first reaches need
             assert 0 <= cy < nch
             p |= pred[idx[(y, cy)]] | (1 << idx[(y, cy)])
         pred[q] = p
-        acc.append(chunk_access(s, b, c, n0, n1))
+        acc.append(chunk_access(s, b, c, n0, n1, ch))
     for a in range(len(inst)):
         ra, wa = acc[a]
         for bq in range(a + 1, len(inst)):
@@ -102,7 +103,7 @@ def test_waits_point_back_and_unordered_chunks_do_not_conflict(n0, n1, T):
             assert not (wb & ra), (inst[a], inst[bq])
 
 
-def run_chunk(state, u, s, b, c, w_desc, cval, shape, n0, n1):
+def run_chunk(state, u, s, b, c, w_desc, cval, shape, n0, n1, ch):
     """One chunk of task (s, b), the lanes' registers emulated as the kernel holds them."""
     RO, RX, O = state
 
@@ -116,7 +117,7 @@ def run_chunk(state, u, s, b, c, w_desc, cval, shape, n0, n1):
             for q in range(-1, 7):
                 RX[k][(q + 8) & 7] = ld(xrow[k], -2 * k + q) if k in (0, 31) else cval
             O[k] = [cval] * 4
-    for tg in range(c * CHUNK, c * CHUNK + CHUNK, 8):
+    for tg in range(c * ch, c * ch + ch, 8):
         for m in range(8):
             outs = []
             for k in range(32):
@@ -156,11 +157,12 @@ def run_chunk(state, u, s, b, c, w_desc, cval, shape, n0, n1):
                 RX[k][(m + 7) & 7] = ld(xrow[k], j + 7) if k in (0, 31) else cval
 
 
+@pytest.mark.parametrize("ch", [32, 64])
 @pytest.mark.parametrize("shape", ["star", "box"])
 @pytest.mark.parametrize("n0,n1,T", [(40, 37, 3), (70, 13, 3), (33, 70, 2), (5, 9, 4)])
-def test_random_orders_that_respect_the_waits_give_the_oracle_result(shape, n0, n1, T):
-    nb, steps, order = geometry(n0, n1, T)
-    nch = steps // CHUNK
+def test_random_orders_that_respect_the_waits_give_the_oracle_result(shape, n0, n1, T, ch):
+    nb, steps, order = geometry(n0, n1, T, ch)
+    nch = steps // ch
     cval = 0.3
     w, u0 = case(2, shape, 1, (n0, n1), seed=n0 + n1)
     w_desc = list(reversed(list(w)))
@@ -174,14 +176,14 @@ def test_random_orders_that_respect_the_waits_give_the_oracle_result(shape, n0, 
     pick = 0
     while True:
         ready = [x for x in order if nxt[x] < nch and
-                 all(prog[y] >= need for y, need in chunk_waits(x[0], x[1], nxt[x] * CHUNK, nb, n1))]
+                 all(prog[y] >= need for y, need in chunk_waits(x[0], x[1], nxt[x] * ch, nb, n1, ch))]
         if not ready:
             break
         x = ready[int(rnd[pick % len(rnd)] * len(ready))]
         pick += 1
-        run_chunk(states[x], u, x[0], x[1], nxt[x], w_desc, cval, shape, n0, n1)
+        run_chunk(states[x], u, x[0], x[1], nxt[x], w_desc, cval, shape, n0, n1, ch)
         nxt[x] += 1
-        prog[x] = nxt[x] * CHUNK
+        prog[x] = nxt[x] * ch
     assert all(nxt[x] == nch for x in order), "the schedule stalled"
     got = u.reshape(u0.shape)
     assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
