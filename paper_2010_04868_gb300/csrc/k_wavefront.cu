@@ -814,20 +814,24 @@ __global__ void k_wave_prefix(WaveGeo wg, int64_t* pre)
 //
 // The same hyperplane order with the roles of the loops exchanged: the lanes
 // of a warp hold 32 consecutive rows of ONE sweep, and the sweeps are
-// pipelined across warps. Lane k updates column j = t - 2k of row 32b + k at
-// step t, so lane k - 1 finished the newest values above a point (columns
-// j - 1 .. j + 1) one to three steps before and hands them over by shuffle,
-// and lane k + 1 has not yet overwritten the old values below it (columns
-// j - 1 .. j + 1 of its own row, which it holds two to four steps ahead of
-// use) and hands those over too. A lane's only memory traffic is its own row:
-// one load (eight columns ahead) and one store per point. Lane 0 reads the
-// newest values of the row above the band from the band above, lane 31 the
-// old values of the row below it from the band below in the previous sweep.
+// pipelined across warps. At step t, lane k updates the four columns of group
+// G = t - SK k (columns 4G .. 4G + 3) of row 32b + k, left to right; lane
+// k - 1 produced the newest values above them (and, for a box, the columns
+// on either side) SK to SK + 1 steps before and hands them over by shuffle,
+// and lane k + 1, which trails by SK groups, has not yet overwritten the old
+// values below them and hands those over too from the groups it holds ahead
+// of use. SK = 1 for the star, 2 for the box (whose above-right neighbour is
+// one group further on). A lane's only memory traffic is its own row: one
+// group of four columns loaded (two 16-byte loads, through L2) and one stored
+// per step, so every sector a warp instruction touches is used whole. Lane 0
+// reads the newest values of the row above the band from the band above,
+// lane 31 the old values of the row below it from the band below in the
+// previous sweep.
 //
 // A task (s, b) is sweep s over band b. It waits (bounded) for the progress
 // words of (s, b - 1) (the row above, this sweep), (s - 1, b) (its own rows,
 // previous sweep) and (s - 1, b + 1) (the row below, previous sweep), once
-// per chunk of CH steps, for exactly the columns the chunk reads, and
+// per chunk of CH steps, for exactly the groups the chunk reads, and
 // publishes its own steps after each chunk. In-place updates are safe: a
 // value is overwritten only by a task that has waited for every reader of the
 // older value (the readers are the tasks it waits for, directly or through
@@ -835,17 +839,17 @@ __global__ void k_wave_prefix(WaveGeo wg, int64_t* pre)
 // task waits for comes earlier, so a persistent kernel whose warps claim
 // tasks from a ticket counter cannot deadlock. The sweeps need no blocking,
 // so no lane idles on a partial block of sweeps; the sum keeps the
-// descending order and rounding of every other kernel.
+// descending order and rounding of every other kernel. Rows of a multiple of
+// four columns only (whole 16-byte-aligned groups).
 constexpr int GR_CHUNK = 32;   // default steps between progress waits and publications (CH)
 constexpr int GR_THREADS = 128;
-constexpr int GR_LAG = 62;     // steps lane 31 trails lane 0 (2 per lane)
 
 struct RowGeo {
-    int64_t n0, n1;   // rows, columns
+    int64_t n0, n1;   // rows, columns (a multiple of 4)
     int64_t nb;       // bands of 32 rows
     int64_t T;        // sweeps of this launch
     int64_t ntasks;   // T * nb
-    int64_t steps;    // steps of a task: n1 + GR_LAG, rounded up to the chunk
+    int64_t steps;    // steps of a task: n1 / 4 + 31 SK, rounded up to the chunk
 };
 
 // The task of ticket tk in the order (s + b, s): (e, pe) is the caller's cursor (anti-diagonal e,
@@ -867,26 +871,6 @@ __device__ __forceinline__ void rows_decode(int64_t tk, const RowGeo& g, int64_t
     }
 }
 
-// Predicated global accesses through L2 without a branch: a lane whose predicate is false touches no
-// memory and (load) keeps the default in its register.
-__device__ __forceinline__ double ldcg_if(const double* p, bool pred, double dflt)
-{
-    double v = dflt;
-    asm volatile(
-        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.cg.f64 %0, [%1];\n\t}"
-        : "+d"(v)
-        : "l"(p), "r"((unsigned)pred)
-        : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void stcg_if(double* p, bool pred, double v)
-{
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.cg.f64 [%0], %1;\n\t}" ::"l"(p),
-                 "d"(v), "r"((unsigned)pred)
-                 : "memory");
-}
-
 // Wait until *p >= need (lane 0); known caches the last value seen. False after a time-out.
 __device__ __forceinline__ bool rows_wait(const int* p, int need, int& known, int spin)
 {
@@ -899,15 +883,63 @@ __device__ __forceinline__ bool rows_wait(const int* p, int need, int& known, in
     return false;
 }
 
+// Four consecutive doubles (a 16-byte-aligned group) through L2, or four times c.
+struct Q4 {
+    double v[4];
+};
+
+__device__ __forceinline__ Q4 ld_group(const double* p, bool ok, double c)
+{
+    Q4 q;
+    if (ok) {
+        const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+        q.v[0] = a.x;
+        q.v[1] = a.y;
+        q.v[2] = b.x;
+        q.v[3] = b.y;
+    } else {
+        q.v[0] = q.v[1] = q.v[2] = q.v[3] = c;
+    }
+    return q;
+}
+
+__device__ __forceinline__ void st_group(double* p, const Q4& q)
+{
+    __stcg(reinterpret_cast<double2*>(p), make_double2(q.v[0], q.v[1]));
+    __stcg(reinterpret_cast<double2*>(p) + 1, make_double2(q.v[2], q.v[3]));
+}
+
+__device__ __forceinline__ Q4 shfl_down4(const Q4& q)
+{
+    Q4 r;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) r.v[e] = __shfl_down_sync(FULL, q.v[e], 1);
+    return r;
+}
+
+__device__ __forceinline__ Q4 shfl_up4(const Q4& q)
+{
+    Q4 r;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) r.v[e] = __shfl_up_sync(FULL, q.v[e], 1);
+    return r;
+}
+
 template <int SHAPE, int ARITH, int CH>
 __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u, RowGeo g, double c,
                                                           WArr<Stn<2, SHAPE, 1>::K> w, int* __restrict__ prog,
                                                           int* __restrict__ ticket, int* status, WaitCfg wc)
 {
+    constexpr int SK = SHAPE == STAR ? 1 : 2;   // groups lane k trails lane k - 1
+    constexpr int QX0 = SHAPE == STAR ? 0 : -1;  // first group of the x-row ring, relative to G
+    constexpr int LX = QX0 + 4;                  // group the x-row ring loads at a step, relative to G
     const int lane = threadIdx.x & 31;
-    const int64_t nprog = g.T * g.nb;
-    const int smax = (int)(g.n1 + GR_LAG);
-    const int n1 = (int)g.n1, steps = (int)g.steps;  // columns and steps fit in int (checked by the host)
+    const int64_t nprog = g.T * g.nb;  // progress words (bounds of the checked build)
+    (void)nprog;
+    const int ng = (int)(g.n1 / 4);
+    const int smax = ng + 31 * SK;  // steps after which every lane has finished its row
+    const int steps = (int)g.steps;
     int64_t e = 0, pe = 0;
     bool timed_out = false;  // after a time-out this warp stops waiting (its results are void anyway)
     for (;;) {
@@ -928,31 +960,29 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
         const bool x_ok = (lane == 0 || lane == 31) && ix >= 0 && ix < g.n0;
         const double* xrow = u + (x_ok ? ix : 0) * g.n1;
         const int64_t f = s * g.nb + b;
-        const int64_t fA = f - 1, fO = f - g.nb, fB = f - g.nb + 1;   // above / own / below predecessors
+        const int64_t fA = f - 1, fO = f - g.nb, fB = f - g.nb + 1;  // above / own / below predecessors
         const bool hasA = b > 0, hasO = s > 0, hasB = s > 0 && b + 1 < g.nb;
         int kA = 0, kO = 0, kB = 0;
-        // grid values written by other SMs: read through L2 (ld.global.cg), never from a stale L1 line;
-        // the predicates keep every access inside the grid (c stands for a value outside it)
-        auto ld_row = [&](int col) -> double {
-            return ldcg_if(row + col, row_ok && (unsigned)col < (unsigned)n1 && GBST_IN(col, n1), c);
+        // grid values written by other SMs are read through L2 (ld.global.cg), never from a stale L1 line
+        auto ld_row = [&](int grp) -> Q4 {
+            return ld_group(row + 4 * (int64_t)grp, row_ok && (unsigned)grp < (unsigned)ng && GBST_IN(grp, ng), c);
         };
-        auto ld_x = [&](int col) -> double {
-            return ldcg_if(xrow + col, x_ok && (unsigned)col < (unsigned)n1 && GBST_IN(col, n1), c);
+        auto ld_x = [&](int grp) -> Q4 {
+            return ld_group(xrow + 4 * (int64_t)grp, x_ok && (unsigned)grp < (unsigned)ng && GBST_IN(grp, ng), c);
         };
-        // RO[(m + q) & 7]: old value of this lane's row at column j + q (q = 0..7), j the column of step m;
-        // RX[(m + q) & 7]: lane 0 the newest row above, lane 31 the old row below, at j + q (q = -1..6);
-        // O[m & 3]: this lane's output of step m (c outside the grid)
-        double RO[8], RX[8], O[4];
+        // RO[(m + q) & 3]: old values of this lane's row, group G + q (q = 0..3), G the group of step m;
+        // RX[(m + q) & 3]: lane 0 the newest row above, lane 31 the old row below, group G + q
+        //                  (q = QX0 .. QX0 + 3);
+        // O[m & 3]: this lane's outputs of step m (c outside the grid)
+        Q4 RO[4], RX[4], O[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) O[q] = c;
+        for (int q = 0; q < 4; ++q) O[q].v[0] = O[q].v[1] = O[q].v[2] = O[q].v[3] = c;
         for (int t0 = 0; t0 < steps; t0 += CH) {
             if (lane == 0 && !timed_out) {
                 bool ok = true;
-                const int nA = t0 + CH + 7 + GR_LAG, nO = t0 + CH + 8, nB = t0 + CH - 55;
-                if (hasA && GBST_IN(fA, nprog))
-                    ok &= rows_wait(prog + fA, nA < smax ? nA : smax, kA, wc.spin);
-                if (ok && hasO && GBST_IN(fO, nprog))
-                    ok &= rows_wait(prog + fO, nO < smax ? nO : smax, kO, wc.spin);
+                const int nA = t0 + CH + LX + 31 * SK, nO = t0 + CH + 4, nB = t0 + CH - 31 * SK + LX;
+                if (hasA && GBST_IN(fA, nprog)) ok &= rows_wait(prog + fA, nA < smax ? nA : smax, kA, wc.spin);
+                if (ok && hasO && GBST_IN(fO, nprog)) ok &= rows_wait(prog + fO, nO < smax ? nO : smax, kO, wc.spin);
                 if (ok && hasB && nB > 0 && GBST_IN(fB, nprog))
                     ok &= rows_wait(prog + fB, nB < smax ? nB : smax, kB, wc.spin);
                 if (!ok) {
@@ -962,62 +992,92 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
             }
             __syncwarp();
             if (t0 == 0) {
-                const int j0 = -2 * lane;
+                const int G0 = -SK * lane;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) RO[q] = ld_row(j0 + q);
+                for (int q = 0; q < 4; ++q) RO[q] = ld_row(G0 + q);
 #pragma unroll
-                for (int q = -1; q < 7; ++q) RX[(q + 8) & 7] = ld_x(j0 + q);
+                for (int q = QX0; q < QX0 + 4; ++q) RX[q & 3] = ld_x(G0 + q);
             }
-            for (int tg = t0; tg < t0 + CH; tg += 8) {
+            for (int tg = t0; tg < t0 + CH; tg += 4) {
 #pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    const int j = tg + m - 2 * lane;
-                    double acc;
+                for (int m = 0; m < 4; ++m) {
+                    const int G = tg + m - SK * lane;
+                    Q4 out;
                     if (SHAPE == STAR) {
-                        // (+1,0) (0,+1) (0,0) (0,-1) (-1,0)
-                        double bel = __shfl_down_sync(FULL, RO[(m + 2) & 7], 1);
-                        double abv = __shfl_up_sync(FULL, O[(m + 2) & 3], 1);
-                        if (lane == 31) bel = RX[m & 7];
-                        if (lane == 0) abv = RX[m & 7];
-                        acc = __dmul_rn(w.w[0], bel);
-                        acc = acc_step<ARITH>(acc, w.w[1], RO[(m + 1) & 7]);
-                        acc = acc_step<ARITH>(acc, w.w[2], RO[m & 7]);
-                        acc = acc_step<ARITH>(acc, w.w[3], O[(m + 3) & 3]);
-                        acc = acc_step<ARITH>(acc, w.w[4], abv);
+                        // below: lane k + 1's own-row group G (its q = 1); above: lane k - 1's outputs of
+                        // step m - 1 (its group then was G); lanes 31 and 0 take the x row's group G
+                        Q4 bel = shfl_down4(RO[(m + 1) & 3]);
+                        Q4 abv = shfl_up4(O[(m + 3) & 3]);
+                        if (lane == 31) bel = RX[m & 3];
+                        if (lane == 0) abv = RX[m & 3];
+                        double left = O[(m + 3) & 3].v[3];
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) {
+                            // (+1,0) (0,+1) (0,0) (0,-1) (-1,0)
+                            const double rgt = x < 3 ? RO[m & 3].v[x + 1] : RO[(m + 1) & 3].v[0];
+                            double acc = __dmul_rn(w.w[0], bel.v[x]);
+                            acc = acc_step<ARITH>(acc, w.w[1], rgt);
+                            acc = acc_step<ARITH>(acc, w.w[2], RO[m & 3].v[x]);
+                            acc = acc_step<ARITH>(acc, w.w[3], left);
+                            acc = acc_step<ARITH>(acc, w.w[4], abv.v[x]);
+                            out.v[x] = acc;
+                            left = acc;
+                        }
                     } else {
-                        // (+1,+1) (+1,0) (+1,-1) (0,+1) (0,0) (0,-1) (-1,+1) (-1,0) (-1,-1)
-                        double br = __shfl_down_sync(FULL, RO[(m + 3) & 7], 1);
-                        double bc = __shfl_down_sync(FULL, RO[(m + 2) & 7], 1);
-                        double bl = __shfl_down_sync(FULL, RO[(m + 1) & 7], 1);
-                        double ar = __shfl_up_sync(FULL, O[(m + 3) & 3], 1);
-                        double ac = __shfl_up_sync(FULL, O[(m + 2) & 3], 1);
-                        double al = __shfl_up_sync(FULL, O[(m + 1) & 3], 1);
+                        // bv[x + 1], av[x + 1]: old row below, newest row above, at column 4G + x
+                        // (x = -1..4); lane k + 1 holds groups G - 1 .. G + 1 as its q = 1..3, lane k - 1
+                        // produced them at steps m - 3 .. m - 1
+                        double bv[6], av[6];
+                        {
+                            const Q4 bc = shfl_down4(RO[(m + 2) & 3]);
+                            const Q4 ac = shfl_up4(O[(m + 2) & 3]);
+                            bv[0] = __shfl_down_sync(FULL, RO[(m + 1) & 3].v[3], 1);
+                            bv[5] = __shfl_down_sync(FULL, RO[(m + 3) & 3].v[0], 1);
+                            av[0] = __shfl_up_sync(FULL, O[(m + 1) & 3].v[3], 1);
+                            av[5] = __shfl_up_sync(FULL, O[(m + 3) & 3].v[0], 1);
+#pragma unroll
+                            for (int x = 0; x < 4; ++x) {
+                                bv[x + 1] = bc.v[x];
+                                av[x + 1] = ac.v[x];
+                            }
+                        }
                         if (lane == 31) {
-                            br = RX[(m + 1) & 7];
-                            bc = RX[m & 7];
-                            bl = RX[(m + 7) & 7];
+                            bv[0] = RX[(m + 3) & 3].v[3];
+                            bv[5] = RX[(m + 1) & 3].v[0];
+#pragma unroll
+                            for (int x = 0; x < 4; ++x) bv[x + 1] = RX[m & 3].v[x];
                         }
                         if (lane == 0) {
-                            ar = RX[(m + 1) & 7];
-                            ac = RX[m & 7];
-                            al = RX[(m + 7) & 7];
+                            av[0] = RX[(m + 3) & 3].v[3];
+                            av[5] = RX[(m + 1) & 3].v[0];
+#pragma unroll
+                            for (int x = 0; x < 4; ++x) av[x + 1] = RX[m & 3].v[x];
                         }
-                        acc = __dmul_rn(w.w[0], br);
-                        acc = acc_step<ARITH>(acc, w.w[1], bc);
-                        acc = acc_step<ARITH>(acc, w.w[2], bl);
-                        acc = acc_step<ARITH>(acc, w.w[3], RO[(m + 1) & 7]);
-                        acc = acc_step<ARITH>(acc, w.w[4], RO[m & 7]);
-                        acc = acc_step<ARITH>(acc, w.w[5], O[(m + 3) & 3]);
-                        acc = acc_step<ARITH>(acc, w.w[6], ar);
-                        acc = acc_step<ARITH>(acc, w.w[7], ac);
-                        acc = acc_step<ARITH>(acc, w.w[8], al);
+                        double left = O[(m + 3) & 3].v[3];
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) {
+                            // (+1,+1) (+1,0) (+1,-1) (0,+1) (0,0) (0,-1) (-1,+1) (-1,0) (-1,-1)
+                            const double rgt = x < 3 ? RO[m & 3].v[x + 1] : RO[(m + 1) & 3].v[0];
+                            double acc = __dmul_rn(w.w[0], bv[x + 2]);
+                            acc = acc_step<ARITH>(acc, w.w[1], bv[x + 1]);
+                            acc = acc_step<ARITH>(acc, w.w[2], bv[x]);
+                            acc = acc_step<ARITH>(acc, w.w[3], rgt);
+                            acc = acc_step<ARITH>(acc, w.w[4], RO[m & 3].v[x]);
+                            acc = acc_step<ARITH>(acc, w.w[5], left);
+                            acc = acc_step<ARITH>(acc, w.w[6], av[x + 2]);
+                            acc = acc_step<ARITH>(acc, w.w[7], av[x + 1]);
+                            acc = acc_step<ARITH>(acc, w.w[8], av[x]);
+                            out.v[x] = acc;
+                            left = acc;
+                        }
                     }
-                    const bool jin = (unsigned)j < (unsigned)n1;
-                    const double out = jin ? acc : c;
+                    const bool gin = (unsigned)G < (unsigned)ng;
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) out.v[x] = gin ? out.v[x] : c;
                     O[m & 3] = out;
-                    stcg_if(row + j, jin && row_ok && GBST_IN(j, n1), out);
-                    RO[m & 7] = ld_row(j + 8);
-                    RX[(m + 7) & 7] = ld_x(j + 7);
+                    if (gin && row_ok && GBST_IN(G, ng)) st_group(row + 4 * (int64_t)G, out);
+                    RO[m & 3] = ld_row(G + 4);
+                    RX[(m + QX0) & 3] = ld_x(G + LX);
                 }
             }
             __syncwarp();
@@ -1504,7 +1564,8 @@ static int launch_sweepdag(const RunCtx& ctx, double* u, const WS& w, const Swee
     return cuda_rc(cudaGetLastError());
 }
 
-// 2D Gauss-Seidel, rows as lanes (k_gs2d_rows): constant boundary, radius 1, constant weights.
+// 2D Gauss-Seidel, rows as lanes (k_gs2d_rows): constant boundary, radius 1, constant weights, rows of
+// a multiple of four columns on a 16-byte-aligned grid (the dispatcher checks).
 // Sweeps go to launches of at most GR_MAX_TASKS tasks (progress words) each.
 constexpr int64_t GR_MAX_TASKS = (int64_t)1 << 24;
 
@@ -1516,8 +1577,9 @@ static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
     g.n0 = ctx.g.n1;
     g.n1 = ctx.g.n2;
     g.nb = (g.n0 + 31) / 32;
-    g.steps = (g.n1 + GR_LAG + CH - 1) / CH * CH;
-    if (g.n1 + GR_LAG + CH > INT32_MAX) return STENCIL_EUNSUPPORTED;  // progress words are int
+    constexpr int SK = SHAPE == STAR ? 1 : 2;
+    g.steps = (g.n1 / 4 + 31 * SK + CH - 1) / CH * CH;
+    if (g.n1 / 4 + 31 * SK + CH > INT32_MAX) return STENCIL_EUNSUPPORTED;  // progress words are int
     const int64_t tmax = GR_MAX_TASKS / g.nb > 0 ? GR_MAX_TASKS / g.nb : 1;
     const int64_t tl = T < tmax ? T : tmax;  // sweeps per launch
     const size_t bytes = 256 + (size_t)(tl * g.nb) * sizeof(int);
@@ -1588,8 +1650,9 @@ static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, boo
         // (measured level with the one-warp tile at best, so not the default)
         const int64_t pw = ctx.wtile[2];
         const bool w8 = pw == 8;
-        // tile[2] = 2: rows as lanes (radius 1, constant weights)
-        if (pw == 2 && h->r == 1 && !ctx.sd.field)
+        // tile[2] = 2: rows as lanes (radius 1, constant weights, whole 16-byte groups of four columns;
+        // other grids take the one-warp tiles)
+        if (pw == 2 && h->r == 1 && !ctx.sd.field && ctx.g.n2 % 4 == 0 && ((uintptr_t)u & 15) == 0)
             return h->shape == STAR ? gs2d_rows<STAR>(ctx, u, T, prep) : gs2d_rows<BOX>(ctx, u, T, prep);
         if (h->shape == STAR && h->r == 1)
             return w8 ? wave_tiles<2, STAR, 1, 8>(ctx, u, T, lanes, prep)

@@ -1,10 +1,11 @@
 """CPU restatement of the rows-as-lanes 2D Gauss-Seidel pipeline (k_gs2d_rows in csrc/k_wavefront.cu).
 
-A task (s, b) is sweep s over band b (32 rows, one per lane); lane k updates column t - 2k at step t.
-Each chunk of ch steps (32 by default, 64 or 128 when a plan asks) first waits for the progress of
-(s, b-1), (s-1, b) and (s-1, b+1), then runs, then publishes. Every load a chunk issues (a lane's own row eight columns ahead, lane 0's row above and
-lane 31's row below seven columns ahead, and the first chunk's ring fill) and every store is placed in
-the chunk that issues it. The checks, on small ragged grids:
+A task (s, b) is sweep s over band b (32 rows, one per lane); at step t lane k updates the group of four
+columns G = t - SK k (SK = 1 for the star, 2 for the box). Each chunk of ch steps (32 by default, 64 or
+128 when a plan asks) first waits for the progress of (s, b-1), (s-1, b) and (s-1, b+1), then runs,
+then publishes. Every load a chunk issues (a lane's own row four groups ahead, lane 0's row above and
+lane 31's row below three or four groups ahead, and the first chunk's ring fill) and every store is
+placed in the chunk that issues it. The checks, on small ragged grids:
   * every wait names a task with an earlier ticket (tickets in the order (s + b, s)), so the
     persistent kernel cannot deadlock;
   * any two chunks the waits (and program order) leave unordered touch disjoint points: neither
@@ -20,21 +21,27 @@ import pytest
 from helpers import case, oracle_run
 from paper_2010_04868_gb300 import inputs
 
-LAG = 62
+
+def params(shape):
+    """(SK, QX0, LX): lane skew in groups, first group of the x-row ring and the group it loads."""
+    return (1, 0, 4) if shape == "star" else (2, -1, 3)
 
 
-def geometry(n0, n1, T, ch):
+def geometry(n0, n1, T, ch, shape):
+    sk = params(shape)[0]
     nb = -(-n0 // 32)
-    steps = -(-(n1 + LAG) // ch) * ch
+    ng = n1 // 4
+    steps = -(-(ng + 31 * sk) // ch) * ch
     order = [(s, e - s) for e in range(T + nb - 1) for s in range(max(0, e - nb + 1), min(T - 1, e) + 1)]
-    return nb, steps, order
+    return nb, ng, steps, order
 
 
-def chunk_waits(s, b, t0, nb, n1, ch):
+def chunk_waits(s, b, t0, nb, ng, ch, shape):
     """(task, progress needed) pairs a chunk starting at step t0 waits for (the kernel's nA, nO, nB)."""
-    smax = n1 + LAG
+    sk, _, lx = params(shape)
+    smax = ng + 31 * sk
     out = []
-    nA, nO, nB = t0 + ch + 7 + LAG, t0 + ch + 8, t0 + ch - 55
+    nA, nO, nB = t0 + ch + lx + 31 * sk, t0 + ch + 4, t0 + ch - 31 * sk + lx
     if b > 0:
         out.append(((s, b - 1), min(nA, smax)))
     if s > 0:
@@ -44,38 +51,41 @@ def chunk_waits(s, b, t0, nb, n1, ch):
     return out
 
 
-def chunk_access(s, b, c, n0, n1, ch):
+def chunk_access(s, b, c, n0, ng, ch, shape):
     """Points a chunk reads and writes."""
+    sk, qx0, lx = params(shape)
     rd, wr = set(), set()
 
-    def add(row, col, into):
-        if 0 <= row < n0 and 0 <= col < n1:
-            into.add((row, col))
+    def add(row, grp, into):
+        if 0 <= row < n0 and 0 <= grp < ng:
+            for x in range(4):
+                into.add((row, 4 * grp + x))
     t0 = c * ch
     if c == 0:
         for k in range(32):
-            for q in range(8):
-                add(32 * b + k, -2 * k + q, rd)
-        for q in range(-1, 7):
+            for q in range(4):
+                add(32 * b + k, -sk * k + q, rd)
+        for q in range(qx0, qx0 + 4):
             add(32 * b - 1, q, rd)
-            add(32 * b + 32, -LAG + q, rd)
+            add(32 * b + 32, -31 * sk + q, rd)
     for t in range(t0, t0 + ch):
         for k in range(32):
-            j = t - 2 * k
-            add(32 * b + k, j, wr)
-            add(32 * b + k, j + 8, rd)
-        add(32 * b - 1, t + 7, rd)
-        add(32 * b + 32, t - LAG + 7, rd)
+            g = t - sk * k
+            add(32 * b + k, g, wr)
+            add(32 * b + k, g + 4, rd)
+        add(32 * b - 1, t + lx, rd)
+        add(32 * b + 32, t - 31 * sk + lx, rd)
     return rd, wr
 
 
-CASES = [(40, 37, 3), (64, 50, 3), (33, 70, 3), (5, 9, 4), (70, 13, 3), (70, 150, 3), (96, 40, 2), (1, 1, 2)]
+CASES = [(40, 36, 3), (64, 52, 3), (33, 68, 3), (5, 8, 4), (70, 12, 3), (70, 152, 3), (96, 40, 2), (1, 4, 2)]
 
 
+@pytest.mark.parametrize("shape", ["star", "box"])
 @pytest.mark.parametrize("ch", [32, 64])
 @pytest.mark.parametrize("n0,n1,T", CASES)
-def test_waits_point_back_and_unordered_chunks_do_not_conflict(n0, n1, T, ch):
-    nb, steps, order = geometry(n0, n1, T, ch)
+def test_waits_point_back_and_unordered_chunks_do_not_conflict(n0, n1, T, ch, shape):
+    nb, ng, steps, order = geometry(n0, n1, T, ch, shape)
     ticket = {x: q for q, x in enumerate(order)}
     nch = steps // ch
     inst = [(x, c) for x in order for c in range(nch)]
@@ -86,13 +96,13 @@ def test_waits_point_back_and_unordered_chunks_do_not_conflict(n0, n1, T, ch):
         p = 0
         if c > 0:
             p |= pred[idx[((s, b), c - 1)]] | (1 << idx[((s, b), c - 1)])
-        for (y, need) in chunk_waits(s, b, c * ch, nb, n1, ch):
+        for (y, need) in chunk_waits(s, b, c * ch, nb, ng, ch, shape):
             assert ticket[y] < ticket[(s, b)], "a wait names a later ticket"
             cy = -(-need // ch) - 1          # the chunk whose publication first reaches need
             assert 0 <= cy < nch
             p |= pred[idx[(y, cy)]] | (1 << idx[(y, cy)])
         pred[q] = p
-        acc.append(chunk_access(s, b, c, n0, n1, ch))
+        acc.append(chunk_access(s, b, c, n0, ng, ch, shape))
     for a in range(len(inst)):
         ra, wa = acc[a]
         for bq in range(a + 1, len(inst)):
@@ -103,22 +113,26 @@ def test_waits_point_back_and_unordered_chunks_do_not_conflict(n0, n1, T, ch):
             assert not (wb & ra), (inst[a], inst[bq])
 
 
-def run_chunk(state, u, s, b, c, w_desc, cval, shape, n0, n1, ch):
-    """One chunk of task (s, b), the lanes' registers emulated as the kernel holds them."""
+def run_chunk(state, u, s, b, c, w_desc, cval, shape, n0, ng, ch):
+    """One chunk of task (s, b), the lanes' registers emulated as the kernel holds them: RO[(m + q) & 3]
+    own-row old group G + q, RX[(m + q) & 3] the x row's group G + q, O[m & 3] the outputs of step m."""
+    sk, qx0, lx = params(shape)
     RO, RX, O = state
-
-    def ld(row, col):
-        return u[row, col] if 0 <= row < n0 and 0 <= col < n1 else cval
     xrow = [32 * b - 1 if k == 0 else 32 * b + 32 for k in range(32)]
+
+    def ld(row, grp):
+        if 0 <= row < n0 and 0 <= grp < ng:
+            return [u[row, 4 * grp + x] for x in range(4)]
+        return [cval] * 4
     if c == 0:
         for k in range(32):
-            for q in range(8):
-                RO[k][q] = ld(32 * b + k, -2 * k + q)
-            for q in range(-1, 7):
-                RX[k][(q + 8) & 7] = ld(xrow[k], -2 * k + q) if k in (0, 31) else cval
-            O[k] = [cval] * 4
-    for tg in range(c * ch, c * ch + ch, 8):
-        for m in range(8):
+            for q in range(4):
+                RO[k][q] = ld(32 * b + k, -sk * k + q)
+            for q in range(qx0, qx0 + 4):
+                RX[k][q & 3] = ld(xrow[k], -sk * k + q) if k in (0, 31) else [cval] * 4
+            O[k] = [[cval] * 4 for _ in range(4)]
+    for tg in range(c * ch, c * ch + ch, 4):
+        for m in range(4):
             outs = []
             for k in range(32):
                 def dn(slot):      # __shfl_down_sync(RO[slot], 1); lane 31 keeps its own value
@@ -126,42 +140,56 @@ def run_chunk(state, u, s, b, c, w_desc, cval, shape, n0, n1, ch):
 
                 def up(slot):      # __shfl_up_sync(O[slot], 1); lane 0 keeps its own value
                     return O[k - 1][slot] if k > 0 else O[k][slot]
+                cen = RO[k][m & 3]
+                rgt = cen[1:] + [RO[k][(m + 1) & 3][0]]
+                left = O[k][(m + 3) & 3][3]
+                out = []
                 if shape == "star":
-                    bel = RX[k][m & 7] if k == 31 else dn((m + 2) & 7)
-                    abv = RX[k][m & 7] if k == 0 else up((m + 2) & 3)
-                    vals = [bel, RO[k][(m + 1) & 7], RO[k][m & 7], O[k][(m + 3) & 3], abv]
+                    bel = RX[k][m & 3] if k == 31 else dn((m + 1) & 3)
+                    abv = RX[k][m & 3] if k == 0 else up((m + 3) & 3)
+                    for x in range(4):
+                        vals = [bel[x], rgt[x], cen[x], left, abv[x]]
+                        a = w_desc[0] * vals[0]
+                        for wq, v in zip(w_desc[1:], vals[1:]):
+                            a = a + wq * v
+                        out.append(a)
+                        left = a
                 else:
                     if k == 31:
-                        br, bc_, bl = RX[k][(m + 1) & 7], RX[k][m & 7], RX[k][(m + 7) & 7]
+                        bv = [RX[k][(m + 3) & 3][3]] + RX[k][m & 3] + [RX[k][(m + 1) & 3][0]]
                     else:
-                        br, bc_, bl = dn((m + 3) & 7), dn((m + 2) & 7), dn((m + 1) & 7)
+                        bv = [dn((m + 1) & 3)[3]] + dn((m + 2) & 3) + [dn((m + 3) & 3)[0]]
                     if k == 0:
-                        ar, ac, al = RX[k][(m + 1) & 7], RX[k][m & 7], RX[k][(m + 7) & 7]
+                        av = [RX[k][(m + 3) & 3][3]] + RX[k][m & 3] + [RX[k][(m + 1) & 3][0]]
                     else:
-                        ar, ac, al = up((m + 3) & 3), up((m + 2) & 3), up((m + 1) & 3)
-                    vals = [br, bc_, bl, RO[k][(m + 1) & 7], RO[k][m & 7], O[k][(m + 3) & 3], ar, ac, al]
-                a = w_desc[0] * vals[0]
-                for wq, v in zip(w_desc[1:], vals[1:]):
-                    a = a + wq * v
-                outs.append(a)
+                        av = [up((m + 1) & 3)[3]] + up((m + 2) & 3) + [up((m + 3) & 3)[0]]
+                    for x in range(4):
+                        vals = [bv[x + 2], bv[x + 1], bv[x], rgt[x], cen[x], left, av[x + 2], av[x + 1], av[x]]
+                        a = w_desc[0] * vals[0]
+                        for wq, v in zip(w_desc[1:], vals[1:]):
+                            a = a + wq * v
+                        out.append(a)
+                        left = a
+                outs.append(out)
             for k in range(32):
-                j = tg + m - 2 * k
-                jin = 0 <= j < n1
-                out = outs[k] if jin else cval
+                g = tg + m - sk * k
+                gin = 0 <= g < ng
+                out = outs[k] if gin else [cval] * 4
                 O[k][m & 3] = out
-                if jin and 32 * b + k < n0:
-                    u[32 * b + k, j] = out
+                if gin and 32 * b + k < n0:
+                    for x in range(4):
+                        u[32 * b + k, 4 * g + x] = out[x]
             for k in range(32):
-                j = tg + m - 2 * k
-                RO[k][m & 7] = ld(32 * b + k, j + 8)
-                RX[k][(m + 7) & 7] = ld(xrow[k], j + 7) if k in (0, 31) else cval
+                g = tg + m - sk * k
+                RO[k][m & 3] = ld(32 * b + k, g + 4)
+                RX[k][(m + qx0) & 3] = ld(xrow[k], g + lx) if k in (0, 31) else [cval] * 4
 
 
 @pytest.mark.parametrize("ch", [32, 64])
 @pytest.mark.parametrize("shape", ["star", "box"])
-@pytest.mark.parametrize("n0,n1,T", [(40, 37, 3), (70, 13, 3), (33, 70, 2), (5, 9, 4)])
+@pytest.mark.parametrize("n0,n1,T", [(40, 36, 3), (70, 12, 3), (33, 68, 2), (5, 8, 4)])
 def test_random_orders_that_respect_the_waits_give_the_oracle_result(shape, n0, n1, T, ch):
-    nb, steps, order = geometry(n0, n1, T, ch)
+    nb, ng, steps, order = geometry(n0, n1, T, ch, shape)
     nch = steps // ch
     cval = 0.3
     w, u0 = case(2, shape, 1, (n0, n1), seed=n0 + n1)
@@ -171,17 +199,16 @@ def test_random_orders_that_respect_the_waits_give_the_oracle_result(shape, n0, 
     u = u0.reshape(n0, n1).copy()
     prog = {x: 0 for x in order}
     nxt = {x: 0 for x in order}
-    states = {x: ([[0.0] * 8 for _ in range(32)], [[0.0] * 8 for _ in range(32)], [[0.0] * 4 for _ in range(32)])
-              for x in order}
+    states = {x: ([[None] * 4 for _ in range(32)], [[None] * 4 for _ in range(32)], [None] * 32) for x in order}
     pick = 0
     while True:
         ready = [x for x in order if nxt[x] < nch and
-                 all(prog[y] >= need for y, need in chunk_waits(x[0], x[1], nxt[x] * ch, nb, n1, ch))]
+                 all(prog[y] >= need for y, need in chunk_waits(x[0], x[1], nxt[x] * ch, nb, ng, ch, shape))]
         if not ready:
             break
         x = ready[int(rnd[pick % len(rnd)] * len(ready))]
         pick += 1
-        run_chunk(states[x], u, x[0], x[1], nxt[x], w_desc, cval, shape, n0, n1, ch)
+        run_chunk(states[x], u, x[0], x[1], nxt[x], w_desc, cval, shape, n0, ng, ch)
         nxt[x] += 1
         prog[x] = nxt[x] * ch
     assert all(nxt[x] == nch for x in order), "the schedule stalled"
