@@ -843,6 +843,7 @@ __global__ void k_wave_prefix(WaveGeo wg, int64_t* pre)
 // four columns only (whole 16-byte-aligned groups).
 constexpr int GR_CHUNK = 32;   // default steps between progress waits and publications (CH)
 constexpr int GR_THREADS = 128;
+constexpr int GR_PSTRIDE = 32;  // ints between two tasks' progress words: one 128-byte line each
 
 struct RowGeo {
     int64_t n0, n1;   // rows, columns (a multiple of 4)
@@ -871,36 +872,40 @@ __device__ __forceinline__ void rows_decode(int64_t tk, const RowGeo& g, int64_t
     }
 }
 
-// Wait until *p >= need (lane 0); known caches the last value seen. False after a time-out.
+// Wait until *p >= need (lane 0); known caches the last value seen. False after a time-out. The
+// back-off grows from 128 ns to 2 us: thousands of warps may be waiting at once, and their polls
+// would otherwise crowd the L2 slices the words (and the grid rows that share them) live in.
 __device__ __forceinline__ bool rows_wait(const int* p, int need, int& known, int spin)
 {
     if (known >= need) return true;
+    unsigned ns = 128;
     for (int it = 0; it < spin; ++it) {
         known = ld_acquire(p);
         if (known >= need) return true;
-        __nanosleep(it < 64 ? 64 : 512);
+        __nanosleep(ns);
+        ns = ns < 2048 ? 2 * ns : 2048;
     }
     return false;
 }
 
-// Four consecutive doubles (a 16-byte-aligned group) through L2, or four times c.
+// Four consecutive doubles (a 16-byte-aligned group) of a row through L2, or four times c where ok
+// is false. Every lane loads (the group index clamped into the row), so that no lane's predicate
+// splits the warp; the value is then selected.
 struct Q4 {
     double v[4];
 };
 
-__device__ __forceinline__ Q4 ld_group(const double* p, bool ok, double c)
+__device__ __forceinline__ Q4 ld_group(const double* rowp, int grp, int ng, bool ok, double c)
 {
+    const int gc = grp < 0 ? 0 : (grp >= ng ? ng - 1 : grp);
+    const double2* p = reinterpret_cast<const double2*>(rowp + 4 * (int64_t)gc);
+    const double2 a = __ldcg(p);
+    const double2 b = __ldcg(p + 1);
     Q4 q;
-    if (ok) {
-        const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
-        const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
-        q.v[0] = a.x;
-        q.v[1] = a.y;
-        q.v[2] = b.x;
-        q.v[3] = b.y;
-    } else {
-        q.v[0] = q.v[1] = q.v[2] = q.v[3] = c;
-    }
+    q.v[0] = ok ? a.x : c;
+    q.v[1] = ok ? a.y : c;
+    q.v[2] = ok ? b.x : c;
+    q.v[3] = ok ? b.y : c;
     return q;
 }
 
@@ -958,17 +963,17 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
         // lane 0: the row above the band (this sweep); lane 31: the row below it (previous sweep)
         const int64_t ix = lane == 0 ? b * 32 - 1 : b * 32 + 32;
         const bool x_ok = (lane == 0 || lane == 31) && ix >= 0 && ix < g.n0;
-        const double* xrow = u + (x_ok ? ix : 0) * g.n1;
+        const double* xrow = x_ok ? u + ix * g.n1 : row;  // other lanes load (and drop) their own row
         const int64_t f = s * g.nb + b;
         const int64_t fA = f - 1, fO = f - g.nb, fB = f - g.nb + 1;  // above / own / below predecessors
         const bool hasA = b > 0, hasO = s > 0, hasB = s > 0 && b + 1 < g.nb;
         int kA = 0, kO = 0, kB = 0;
         // grid values written by other SMs are read through L2 (ld.global.cg), never from a stale L1 line
         auto ld_row = [&](int grp) -> Q4 {
-            return ld_group(row + 4 * (int64_t)grp, row_ok && (unsigned)grp < (unsigned)ng && GBST_IN(grp, ng), c);
+            return ld_group(row, grp, ng, row_ok && (unsigned)grp < (unsigned)ng && GBST_IN(grp, ng), c);
         };
         auto ld_x = [&](int grp) -> Q4 {
-            return ld_group(xrow + 4 * (int64_t)grp, x_ok && (unsigned)grp < (unsigned)ng && GBST_IN(grp, ng), c);
+            return ld_group(xrow, grp, ng, x_ok && (unsigned)grp < (unsigned)ng && GBST_IN(grp, ng), c);
         };
         // RO[(m + q) & 3]: old values of this lane's row, group G + q (q = 0..3), G the group of step m;
         // RX[(m + q) & 3]: lane 0 the newest row above, lane 31 the old row below, group G + q
@@ -981,10 +986,12 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
             if (lane == 0 && !timed_out) {
                 bool ok = true;
                 const int nA = t0 + CH + LX + 31 * SK, nO = t0 + CH + 4, nB = t0 + CH - 31 * SK + LX;
-                if (hasA && GBST_IN(fA, nprog)) ok &= rows_wait(prog + fA, nA < smax ? nA : smax, kA, wc.spin);
-                if (ok && hasO && GBST_IN(fO, nprog)) ok &= rows_wait(prog + fO, nO < smax ? nO : smax, kO, wc.spin);
+                if (hasA && GBST_IN(fA, nprog))
+                    ok &= rows_wait(prog + fA * GR_PSTRIDE, nA < smax ? nA : smax, kA, wc.spin);
+                if (ok && hasO && GBST_IN(fO, nprog))
+                    ok &= rows_wait(prog + fO * GR_PSTRIDE, nO < smax ? nO : smax, kO, wc.spin);
                 if (ok && hasB && nB > 0 && GBST_IN(fB, nprog))
-                    ok &= rows_wait(prog + fB, nB < smax ? nB : smax, kB, wc.spin);
+                    ok &= rows_wait(prog + fB * GR_PSTRIDE, nB < smax ? nB : smax, kB, wc.spin);
                 if (!ok) {
                     atomicExch(status, DEV_TIMEOUT);
                     timed_out = true;
@@ -1083,7 +1090,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
             __syncwarp();
             if (lane == 0 && publish && GBST_IN(f, nprog)) {
                 __threadfence();
-                st_release(prog + f, t0 + CH);
+                st_release(prog + f * GR_PSTRIDE, t0 + CH);
             }
         }
     }
@@ -1567,7 +1574,7 @@ static int launch_sweepdag(const RunCtx& ctx, double* u, const WS& w, const Swee
 // 2D Gauss-Seidel, rows as lanes (k_gs2d_rows): constant boundary, radius 1, constant weights, rows of
 // a multiple of four columns on a 16-byte-aligned grid (the dispatcher checks).
 // Sweeps go to launches of at most GR_MAX_TASKS tasks (progress words) each.
-constexpr int64_t GR_MAX_TASKS = (int64_t)1 << 24;
+constexpr int64_t GR_MAX_TASKS = (int64_t)1 << 20;
 
 template <int SHAPE, int CH>
 static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
@@ -1582,7 +1589,7 @@ static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
     if (g.n1 / 4 + 31 * SK + CH > INT32_MAX) return STENCIL_EUNSUPPORTED;  // progress words are int
     const int64_t tmax = GR_MAX_TASKS / g.nb > 0 ? GR_MAX_TASKS / g.nb : 1;
     const int64_t tl = T < tmax ? T : tmax;  // sweeps per launch
-    const size_t bytes = 256 + (size_t)(tl * g.nb) * sizeof(int);
+    const size_t bytes = 256 + (size_t)(tl * g.nb) * GR_PSTRIDE * sizeof(int);
     int rc = wave_workspace(h, bytes, ctx.st);
     if (rc || prepare_only) return rc;
     int* ticket = (int*)h->wave_ws;
@@ -1608,7 +1615,8 @@ static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
         const int64_t need = (g.ntasks + GR_THREADS / 32 - 1) / (GR_THREADS / 32);
         if (nblk > need) nblk = need;
         if (cudaMemsetAsync(ticket, 0, 8, ctx.st) != cudaSuccess) return STENCIL_ECUDA;
-        if (cudaMemsetAsync(prog, 0, (size_t)g.ntasks * sizeof(int), ctx.st) != cudaSuccess) return STENCIL_ECUDA;
+        if (cudaMemsetAsync(prog, 0, (size_t)g.ntasks * GR_PSTRIDE * sizeof(int), ctx.st) != cudaSuccess)
+            return STENCIL_ECUDA;
         kern<<<(unsigned)nblk, GR_THREADS, 0, ctx.st>>>(u, g, h->c, w, prog, ticket, h->d_status, wc);
         g_launches++;
         if (cudaGetLastError() != cudaSuccess) return STENCIL_ECUDA;
@@ -1616,10 +1624,11 @@ static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
     return STENCIL_OK;
 }
 
-// steps per chunk of the rows pipeline: 32, or 64 / 128 when the wavefront plan asks (tile[1])
+// steps per chunk of the rows pipeline: 32, or 16 / 64 / 128 when the wavefront plan asks (tile[1])
 template <int SHAPE>
 static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
 {
+    if (ctx.wtile[1] == 16) return gs2d_rows<SHAPE, 16>(ctx, u, T, prepare_only);
     if (ctx.wtile[1] == 64) return gs2d_rows<SHAPE, 64>(ctx, u, T, prepare_only);
     if (ctx.wtile[1] == 128) return gs2d_rows<SHAPE, 128>(ctx, u, T, prepare_only);
     return gs2d_rows<SHAPE, GR_CHUNK>(ctx, u, T, prepare_only);
