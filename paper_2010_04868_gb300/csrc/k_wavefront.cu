@@ -1624,10 +1624,11 @@ static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
     return STENCIL_OK;
 }
 
-// steps per chunk of the rows pipeline: 32, or 16 / 64 / 128 when the wavefront plan asks (tile[1])
+// steps per chunk of the rows pipeline: 32, or 8 / 16 / 64 / 128 when the wavefront plan asks (tile[1])
 template <int SHAPE>
 static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
 {
+    if (ctx.wtile[1] == 8) return gs2d_rows<SHAPE, 8>(ctx, u, T, prepare_only);
     if (ctx.wtile[1] == 16) return gs2d_rows<SHAPE, 16>(ctx, u, T, prepare_only);
     if (ctx.wtile[1] == 64) return gs2d_rows<SHAPE, 64>(ctx, u, T, prepare_only);
     if (ctx.wtile[1] == 128) return gs2d_rows<SHAPE, 128>(ctx, u, T, prepare_only);

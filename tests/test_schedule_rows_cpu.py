@@ -1,8 +1,8 @@
 """CPU restatement of the rows-as-lanes 2D Gauss-Seidel pipeline (k_gs2d_rows in csrc/k_wavefront.cu).
 
 A task (s, b) is sweep s over band b (32 rows, one per lane); at step t lane k updates the group of four
-columns G = t - SK k (SK = 1 for the star, 2 for the box). Each chunk of ch steps (32 by default, 16, 64
-or 128 when a plan asks) first waits for the progress of (s, b-1), (s-1, b) and (s-1, b+1), then runs,
+columns G = t - SK k (SK = 1 for the star, 2 for the box). Each chunk of ch steps (32 by default; 8, 16,
+64 or 128 when a plan asks) first waits for the progress of (s, b-1), (s-1, b) and (s-1, b+1), then runs,
 then publishes. Every load a chunk issues (a lane's own row four groups ahead, lane 0's row above and
 lane 31's row below three or four groups ahead, and the first chunk's ring fill) and every store is
 placed in the chunk that issues it. The checks, on small ragged grids:
@@ -82,7 +82,7 @@ CASES = [(40, 36, 3), (64, 52, 3), (33, 68, 3), (5, 8, 4), (70, 12, 3), (70, 152
 
 
 @pytest.mark.parametrize("shape", ["star", "box"])
-@pytest.mark.parametrize("ch", [16, 32, 64])
+@pytest.mark.parametrize("ch", [8, 16, 32, 64])
 @pytest.mark.parametrize("n0,n1,T", CASES)
 def test_waits_point_back_and_unordered_chunks_do_not_conflict(n0, n1, T, ch, shape):
     nb, ng, steps, order = geometry(n0, n1, T, ch, shape)
@@ -185,7 +185,7 @@ def run_chunk(state, u, s, b, c, w_desc, cval, shape, n0, ng, ch):
                 RX[k][(m + qx0) & 3] = ld(xrow[k], g + lx) if k in (0, 31) else [cval] * 4
 
 
-@pytest.mark.parametrize("ch", [16, 32, 64])
+@pytest.mark.parametrize("ch", [8, 16, 32, 64])
 @pytest.mark.parametrize("shape", ["star", "box"])
 @pytest.mark.parametrize("n0,n1,T", [(40, 36, 3), (70, 12, 3), (33, 68, 2), (5, 8, 4)])
 def test_random_orders_that_respect_the_waits_give_the_oracle_result(shape, n0, n1, T, ch):
