@@ -120,7 +120,7 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
  *            (one weight per term: a warp's lanes hold 32 rows of one sweep,
  *            the sweeps pipelined across warps; tile[0] = CTAs of four
  *            warps per SM, tile[1] = steps between progress publications,
- *            8, 16, 32 (default), 64 or 128); for WAVEFRONT with a
+ *            8 (default), 16, 64 or 128); for WAVEFRONT with a
  *            periodic boundary (the in-sweep tile DAG), tile[0] and tile[1] =
  *            lines per tile along axes 0 (3D) and 1, one thread each, at most
  *            256 in all, and tile[2] = hyperplane steps per tile; for STREAM,

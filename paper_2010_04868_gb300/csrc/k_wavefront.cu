@@ -841,7 +841,7 @@ __global__ void k_wave_prefix(WaveGeo wg, int64_t* pre)
 // so no lane idles on a partial block of sweeps; the sum keeps the
 // descending order and rounding of every other kernel. Rows of a multiple of
 // four columns only (whole 16-byte-aligned groups).
-constexpr int GR_CHUNK = 32;   // default steps between progress waits and publications (CH)
+constexpr int GR_CHUNK = 8;    // default steps between progress waits and publications (CH)
 constexpr int GR_THREADS = 128;
 constexpr int GR_PSTRIDE = 32;  // ints between two tasks' progress words: one 128-byte line each
 
@@ -873,17 +873,17 @@ __device__ __forceinline__ void rows_decode(int64_t tk, const RowGeo& g, int64_t
 }
 
 // Wait until *p >= need (lane 0); known caches the last value seen. False after a time-out. The
-// back-off grows from 128 ns to 2 us: thousands of warps may be waiting at once, and their polls
-// would otherwise crowd the L2 slices the words (and the grid rows that share them) live in.
+// sleep between polls follows the distance still to go (about 0.25 us per missing step, 64 ns to
+// 4 us): a producer a step or two short is seen soon after it publishes, while the thousands of
+// warps whose producers are far behind poll rarely and leave the L2 slices alone.
 __device__ __forceinline__ bool rows_wait(const int* p, int need, int& known, int spin)
 {
     if (known >= need) return true;
-    unsigned ns = 128;
     for (int it = 0; it < spin; ++it) {
         known = ld_acquire(p);
         if (known >= need) return true;
-        __nanosleep(ns);
-        ns = ns < 2048 ? 2 * ns : 2048;
+        const int gap = need - known;
+        __nanosleep(gap < 1 ? 64u : (gap > 16 ? 4096u : 256u * (unsigned)gap));
     }
     return false;
 }
@@ -1624,15 +1624,14 @@ static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
     return STENCIL_OK;
 }
 
-// steps per chunk of the rows pipeline: 32, or 8 / 16 / 64 / 128 when the wavefront plan asks (tile[1])
+// steps per chunk of the rows pipeline: 8, or 16 / 64 / 128 when the wavefront plan asks (tile[1])
 template <int SHAPE>
 static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
 {
-    if (ctx.wtile[1] == 8) return gs2d_rows<SHAPE, 8>(ctx, u, T, prepare_only);
     if (ctx.wtile[1] == 16) return gs2d_rows<SHAPE, 16>(ctx, u, T, prepare_only);
     if (ctx.wtile[1] == 64) return gs2d_rows<SHAPE, 64>(ctx, u, T, prepare_only);
     if (ctx.wtile[1] == 128) return gs2d_rows<SHAPE, 128>(ctx, u, T, prepare_only);
-    return gs2d_rows<SHAPE, GR_CHUNK>(ctx, u, T, prepare_only);
+    return gs2d_rows<SHAPE, GR_CHUNK>(ctx, u, T, prepare_only);  // 8 steps
 }
 
 static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, bool prep)

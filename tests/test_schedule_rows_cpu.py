@@ -1,8 +1,8 @@
 """CPU restatement of the rows-as-lanes 2D Gauss-Seidel pipeline (k_gs2d_rows in csrc/k_wavefront.cu).
 
 A task (s, b) is sweep s over band b (32 rows, one per lane); at step t lane k updates the group of four
-columns G = t - SK k (SK = 1 for the star, 2 for the box). Each chunk of ch steps (32 by default; 8, 16,
-64 or 128 when a plan asks) first waits for the progress of (s, b-1), (s-1, b) and (s-1, b+1), then runs,
+columns G = t - SK k (SK = 1 for the star, 2 for the box). Each chunk of ch steps (8 by default; 16, 64 or
+128 when a plan asks) first waits for the progress of (s, b-1), (s-1, b) and (s-1, b+1), then runs,
 then publishes. Every load a chunk issues (a lane's own row four groups ahead, lane 0's row above and
 lane 31's row below three or four groups ahead, and the first chunk's ring fill) and every store is
 placed in the chunk that issues it. The checks, on small ragged grids:
