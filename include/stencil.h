@@ -113,14 +113,16 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
  *            (slowest first) for DIAMOND; for WAVEFRONT in 2D/3D with a
  *            constant boundary, tile[0] = CTAs per SM of the persistent
  *            kernel, in 2D tile[1] = skewed rows per tile (2..64) and, in 2D
- *            with radius 1, tile[2] = points per lane and step of the
- *            one-warp tile (8 or 16), 1 for the decoupled tile of the
- *            5-point star with one weight per term (a chain warp, producer
- *            warps and a scheduler warp per tile), or 2 for rows as lanes
- *            (one weight per term: a warp's lanes hold 32 rows of one sweep,
- *            the sweeps pipelined across warps; tile[0] = CTAs of four
- *            warps per SM, tile[1] = steps between progress publications,
- *            8 (default), 16, 64 or 128); for WAVEFRONT with a
+ *            with radius 1, tile[2] = 0 (default) or 2 for rows as lanes
+ *            where they apply (one weight per term, rows of a multiple of 4
+ *            columns, a 32-byte-aligned grid: a warp's lanes hold 32 rows of
+ *            one sweep, the sweeps pipelined across warps; tile[0] = CTAs of
+ *            four warps per SM, tile[1] = steps between progress
+ *            publications, 8 (default), 16, 64 or 128), 8 or 16 for the
+ *            points per lane and step of the one-warp tile (the default
+ *            elsewhere, with 16), 1 for the decoupled tile of the 5-point
+ *            star with one weight per term (a chain warp, producer warps and
+ *            a scheduler warp per tile); for WAVEFRONT with a
  *            periodic boundary (the in-sweep tile DAG), tile[0] and tile[1] =
  *            lines per tile along axes 0 (3D) and 1, one thread each, at most
  *            256 in all, and tile[2] = hyperplane steps per tile; for STREAM,

@@ -822,7 +822,7 @@ __global__ void k_wave_prefix(WaveGeo wg, int64_t* pre)
 // values below them and hands those over too from the groups it holds ahead
 // of use. SK = 1 for the star, 2 for the box (whose above-right neighbour is
 // one group further on). A lane's only memory traffic is its own row: one
-// group of four columns loaded (two 16-byte loads, through L2) and one stored
+// group of four columns loaded (one 32-byte sector, through L2) and one stored
 // per step, so every sector a warp instruction touches is used whole. Lane 0
 // reads the newest values of the row above the band from the band above,
 // lane 31 the old values of the row below it from the band below in the
@@ -840,7 +840,7 @@ __global__ void k_wave_prefix(WaveGeo wg, int64_t* pre)
 // tasks from a ticket counter cannot deadlock. The sweeps need no blocking,
 // so no lane idles on a partial block of sweeps; the sum keeps the
 // descending order and rounding of every other kernel. Rows of a multiple of
-// four columns only (whole 16-byte-aligned groups).
+// four columns only (whole 32-byte-aligned groups).
 constexpr int GR_CHUNK = 8;    // default steps between progress waits and publications (CH)
 constexpr int GR_THREADS = 128;
 constexpr int GR_PSTRIDE = 32;  // ints between two tasks' progress words: one 128-byte line each
@@ -872,7 +872,8 @@ __device__ __forceinline__ void rows_decode(int64_t tk, const RowGeo& g, int64_t
     }
 }
 
-// Wait until *p >= need (lane 0); known caches the last value seen. False after a time-out. The
+// Wait until *p >= need (all lanes of the warp); known caches the last value seen. False after a
+// time-out. The
 // sleep between polls follows the distance still to go (about 0.25 us per missing step, 64 ns to
 // 4 us): a producer a step or two short is seen soon after it publishes, while the thousands of
 // warps whose producers are far behind poll rarely and leave the L2 slices alone.
@@ -880,7 +881,7 @@ __device__ __forceinline__ bool rows_wait(const int* p, int need, int& known, in
 {
     if (known >= need) return true;
     for (int it = 0; it < spin; ++it) {
-        known = ld_acquire(p);
+        known = __shfl_sync(FULL, ld_acquire(p), 0);  // lane 0's value: the loop stays uniform
         if (known >= need) return true;
         const int gap = need - known;
         __nanosleep(gap < 1 ? 64u : (gap > 16 ? 4096u : 256u * (unsigned)gap));
@@ -888,9 +889,11 @@ __device__ __forceinline__ bool rows_wait(const int* p, int need, int& known, in
     return false;
 }
 
-// Four consecutive doubles (a 16-byte-aligned group) of a row through L2, or four times c where ok
-// is false. Every lane loads (the group index clamped into the row), so that no lane's predicate
-// splits the warp; the value is then selected.
+// Four consecutive doubles (a 32-byte-aligned group, one sector) of a row through L2, or four times
+// c where ok is false. Every lane loads (the group index clamped into the row), so that no lane's
+// predicate splits the warp; the value is then selected. Groups move as whole sectors (256-bit
+// accesses): a sector written in two halves by separate stores was measured to make its later
+// reads several times slower.
 struct Q4 {
     double v[4];
 };
@@ -898,21 +901,22 @@ struct Q4 {
 __device__ __forceinline__ Q4 ld_group(const double* rowp, int grp, int ng, bool ok, double c)
 {
     const int gc = grp < 0 ? 0 : (grp >= ng ? ng - 1 : grp);
-    const double2* p = reinterpret_cast<const double2*>(rowp + 4 * (int64_t)gc);
-    const double2 a = __ldcg(p);
-    const double2 b = __ldcg(p + 1);
+    const double* p = rowp + 4 * (int64_t)gc;
+    double a, b2, e, d;
+    asm volatile("ld.global.cg.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(a), "=d"(b2), "=d"(e), "=d"(d) : "l"(p) : "memory");
     Q4 q;
-    q.v[0] = ok ? a.x : c;
-    q.v[1] = ok ? a.y : c;
-    q.v[2] = ok ? b.x : c;
-    q.v[3] = ok ? b.y : c;
+    q.v[0] = ok ? a : c;
+    q.v[1] = ok ? b2 : c;
+    q.v[2] = ok ? e : c;
+    q.v[3] = ok ? d : c;
     return q;
 }
 
 __device__ __forceinline__ void st_group(double* p, const Q4& q)
 {
-    __stcg(reinterpret_cast<double2*>(p), make_double2(q.v[0], q.v[1]));
-    __stcg(reinterpret_cast<double2*>(p) + 1, make_double2(q.v[2], q.v[3]));
+    asm volatile("st.global.cg.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(q.v[0]), "d"(q.v[1]), "d"(q.v[2]),
+                 "d"(q.v[3])
+                 : "memory");
 }
 
 __device__ __forceinline__ Q4 shfl_down4(const Q4& q)
@@ -983,7 +987,9 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
 #pragma unroll
         for (int q = 0; q < 4; ++q) O[q].v[0] = O[q].v[1] = O[q].v[2] = O[q].v[3] = c;
         for (int t0 = 0; t0 < steps; t0 += CH) {
-            if (lane == 0 && !timed_out) {
+            // every lane polls (one warp-wide load of one word, the same value to all lanes), so that
+            // the warp never splits around the wait; timed_out stays uniform
+            if (!timed_out) {
                 bool ok = true;
                 const int nA = t0 + CH + LX + 31 * SK, nO = t0 + CH + 4, nB = t0 + CH - 31 * SK + LX;
                 if (hasA && GBST_IN(fA, nprog))
@@ -992,8 +998,9 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
                     ok &= rows_wait(prog + fO * GR_PSTRIDE, nO < smax ? nO : smax, kO, wc.spin);
                 if (ok && hasB && nB > 0 && GBST_IN(fB, nprog))
                     ok &= rows_wait(prog + fB * GR_PSTRIDE, nB < smax ? nB : smax, kB, wc.spin);
+                ok = __all_sync(FULL, ok);
                 if (!ok) {
-                    atomicExch(status, DEV_TIMEOUT);
+                    if (lane == 0) atomicExch(status, DEV_TIMEOUT);
                     timed_out = true;
                 }
             }
@@ -1572,7 +1579,7 @@ static int launch_sweepdag(const RunCtx& ctx, double* u, const WS& w, const Swee
 }
 
 // 2D Gauss-Seidel, rows as lanes (k_gs2d_rows): constant boundary, radius 1, constant weights, rows of
-// a multiple of four columns on a 16-byte-aligned grid (the dispatcher checks).
+// a multiple of four columns on a 32-byte-aligned grid (the dispatcher checks).
 // Sweeps go to launches of at most GR_MAX_TASKS tasks (progress words) each.
 constexpr int64_t GR_MAX_TASKS = (int64_t)1 << 20;
 
@@ -1659,9 +1666,11 @@ static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, boo
         // (measured level with the one-warp tile at best, so not the default)
         const int64_t pw = ctx.wtile[2];
         const bool w8 = pw == 8;
-        // tile[2] = 2: rows as lanes (radius 1, constant weights, whole 16-byte groups of four columns;
-        // other grids take the one-warp tiles)
-        if (pw == 2 && h->r == 1 && !ctx.sd.field && ctx.g.n2 % 4 == 0 && ((uintptr_t)u & 15) == 0)
+        // tile[2] = 0 (default) or 2: rows as lanes where they apply (radius 1, constant weights, rows of
+        // whole 32-byte groups of four columns); 16 or 8: the one-warp tiles with that many points per
+        // lane and step; 1: the decoupled tile. Other grids take the one-warp tiles.
+        const bool rows_ok = h->r == 1 && !ctx.sd.field && ctx.g.n2 % 4 == 0 && ((uintptr_t)u & 31) == 0;
+        if ((pw == 0 || pw == 2) && rows_ok)
             return h->shape == STAR ? gs2d_rows<STAR>(ctx, u, T, prep) : gs2d_rows<BOX>(ctx, u, T, prep);
         if (h->shape == STAR && h->r == 1)
             return w8 ? wave_tiles<2, STAR, 1, 8>(ctx, u, T, lanes, prep)

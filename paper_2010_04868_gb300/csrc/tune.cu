@@ -180,6 +180,7 @@ std::vector<Plan> gs_candidates(const stencil_handle_s* h)
         add(3, 8, 16);
         if (h->r == 1) add(2, 32, 8);
         if (h->r == 1 && h->shape == STAR && !h->field) add(3, 32, 1);   // the decoupled tile
+        if (h->r == 1 && !h->field) add(2, 0, 2);                         // rows as lanes, 2 CTAs per SM
     } else {
         add(3, 0, 0);
         add(4, 0, 0);
