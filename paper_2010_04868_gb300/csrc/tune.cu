@@ -180,7 +180,6 @@ std::vector<Plan> gs_candidates(const stencil_handle_s* h)
         add(3, 8, 16);
         if (h->r == 1) add(2, 32, 8);
         if (h->r == 1 && h->shape == STAR && !h->field) add(3, 32, 1);   // the decoupled tile
-        if (h->r == 1 && !h->field) add(2, 0, 2);                         // rows as lanes, 2 CTAs per SM
     } else {
         add(3, 0, 0);
         add(4, 0, 0);
@@ -274,7 +273,9 @@ Plan plan_for(const stencil_handle_s* hc, const Geo& g, int64_t T, cudaStream_t 
     if (h->dim == 3) { ext[0] = g.n0; ext[1] = g.n1; ext[2] = g.n2; }
     // probe length: enough steps to amortise a pass of the deepest candidate, bounded by T
     int64_t probe = h->dim == 1 ? 128 : (h->dim == 2 ? 48 : 8);
-    if (gs_tuned) probe = h->dim == 2 ? 64 : 32;   // two sweep blocks of the wavefront
+    // two sweep blocks of the one-warp tiles; in 2D enough sweeps that the rows-as-lanes pipeline's
+    // fill (a fixed number of steps) does not decide the choice
+    if (gs_tuned) probe = h->dim == 2 ? 128 : 32;
     if (probe > T) probe = T;
     std::vector<Plan> cands = gs_tuned ? gs_candidates(h) : jacobi_candidates(h, g, T);
     // the plain kernel is the reference: another plan must beat it by a clear
