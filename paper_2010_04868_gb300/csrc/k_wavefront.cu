@@ -86,17 +86,18 @@ __device__ __forceinline__ void st_release64(unsigned long long* p, unsigned lon
 constexpr int PROG_SHIFT = 40;
 constexpr unsigned long long PROG_MASK = (1ull << PROG_SHIFT) - 1;
 
-// Wait until the previous block has finalised positions [0, need); returns how
-// many it has (a large value after a time-out, which is recorded in status).
-__device__ __noinline__ int64_t wait_progress(const unsigned long long* p, int64_t need, unsigned tag, int* status,
-                                              int spin)
+// Wait until the previous block has finalised positions [0, need); returns how many it has (a large
+// value after a time-out, which is recorded in status). Run by a whole warp: every lane polls and
+// lane 0's value is broadcast, so that the warp never splits around the wait.
+__device__ __forceinline__ int64_t wait_progress_warp(const unsigned long long* p, int64_t need, unsigned tag,
+                                                      int* status, int spin)
 {
     for (int it = 0; it < spin; ++it) {
-        unsigned long long v = ld_acquire64(p);
+        const unsigned long long v = __shfl_sync(0xffffffffu, ld_acquire64(p), 0);
         if ((unsigned)(v >> PROG_SHIFT) == tag && (int64_t)(v & PROG_MASK) >= need) return (int64_t)(v & PROG_MASK);
         __nanosleep(500);
     }
-    atomicExch(status, DEV_TIMEOUT);
+    if ((threadIdx.x & 31) == 0) atomicExch(status, DEV_TIMEOUT);
     return INT64_MAX;
 }
 
@@ -130,8 +131,7 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
     // to lane 0 by shuffle, so no load latency sits on the step's critical path.
     auto need_upto = [&](int64_t upto) {
         // positions [0, upto) must be final in the previous block's output
-        if (lane == 0 && upto > known) known = wait_progress(prev, upto, tag, status, wc.spin);
-        __syncwarp();
+        if (upto > known) known = wait_progress_warp(prev, upto, tag, status, wc.spin);  // the warp as one
     };
     auto load_chunk = [&](int64_t ch) -> double {
         const int64_t p = ch * 32 + lane;
@@ -297,8 +297,7 @@ __global__ void __launch_bounds__(256) k_gs1d_wave4(double* __restrict__ u, int6
         const int64_t lo = W4_D * m;
         if (lo >= n) return;
         const int64_t need = lo + 32 < n ? lo + 32 : n;
-        if (lane == 0 && need > known) known = wait_progress(prev, need, tag, status, wc.spin);
-        __syncwarp();
+        if (need > known) known = wait_progress_warp(prev, need, tag, status, wc.spin);  // warp 7 as one
         const int64_t x = lo + lane;
         double* dst = BOT + (x & 63);
         if (x < n) {
@@ -498,6 +497,20 @@ __device__ __forceinline__ bool wait_flag_ge_at(const int* flags, int64_t f, int
 __device__ __forceinline__ void release_flag_at(int* flags, int64_t f, int64_t n, int tag)
 {
     if (GBST_IN(f, n)) st_release(flags + f, tag);
+}
+
+// The same wait run by a whole warp: every lane polls, and lane 0's value is broadcast, so that all
+// lanes leave the loop together and the warp never splits around the wait (a warp whose lane 0 alone
+// polled while the others waited at a barrier was measured to run its following work several times
+// slower).
+__device__ __forceinline__ bool wait_flag_ge_warp_at(const int* flags, int64_t f, int64_t n, int tag, int spin)
+{
+    if (!GBST_IN(f, n)) return true;
+    for (int it = 0; it < spin; ++it) {
+        if (__shfl_sync(FULL, ld_acquire(flags + f), 0) >= tag) return true;
+        __nanosleep(it < 64 ? 32 : 256);
+    }
+    return false;
 }
 
 // Which window cells a point update reads: every cell for a box; for a star
@@ -1198,10 +1211,14 @@ __global__ void __launch_bounds__(256) k_gs_sweepdag(double* __restrict__ u, Geo
     const int64_t total = t.sweep_units * t.T;
     const int64_t s1 = g.n2, s0 = g.n1 * g.n2;
     for (;;) {
-        if (threadIdx.x == 0) {
-            const long long tk = (long long)atomicAdd(ticket, 1ull);
-            s_go = tk < total;
-            if (s_go) {
+        if (threadIdx.x < 32) {
+            // warp 0 claims the next tile and waits for it, all of its lanes together
+            const int lane = threadIdx.x;
+            long long tk = 0;
+            if (lane == 0) tk = (long long)atomicAdd(ticket, 1ull);
+            tk = __shfl_sync(FULL, tk, 0);
+            if (lane == 0) s_go = tk < total;
+            if (tk < total) {
                 const int64_t sw = tk / t.sweep_units, rem = tk % t.sweep_units;
                 int64_t lo = 0, hi = t.Dn - 1;
                 while (lo < hi) {
@@ -1223,10 +1240,12 @@ __global__ void __launch_bounds__(256) k_gs_sweepdag(double* __restrict__ u, Geo
                     r -= cnt;
                 }
                 const int64_t TS = D - T0 - T1;
-                s_T0 = T0;
-                s_T1 = T1;
-                s_TS = TS;
-                s_sw = sw;
+                if (lane == 0) {
+                    s_T0 = T0;
+                    s_T1 = T1;
+                    s_TS = TS;
+                    s_sw = sw;
+                }
                 // the three lower neighbours of this sweep, then what this tile needs of the previous
                 // sweep (sweep_dag_prev_waits)
                 bool ok = true;
@@ -1235,12 +1254,13 @@ __global__ void __launch_bounds__(256) k_gs_sweepdag(double* __restrict__ u, Geo
                 if (sw > 0) {
                     int64_t pw[4];
                     const int np = sweep_dag_prev_waits<DIM, R>(t, g, T0, T1, TS, pw);
-                    for (int q = 0; q < np; ++q) ok &= wait_flag_ge_at(flags, pw[q], t.sweep_units, (int)sw, wc.spin);
+                    for (int q = 0; q < np; ++q)
+                        ok &= wait_flag_ge_warp_at(flags, pw[q], t.sweep_units, (int)sw, wc.spin);
                 }
-                if (T0 > 0) ok &= wait_flag_ge_at(flags, f - t.nt1 * t.nts, t.sweep_units, tag, wc.spin);
-                if (T1 > 0) ok &= wait_flag_ge_at(flags, f - t.nts, t.sweep_units, tag, wc.spin);
-                if (TS > 0) ok &= wait_flag_ge_at(flags, f - 1, t.sweep_units, tag, wc.spin);
-                if (!ok) atomicExch(status, DEV_TIMEOUT);
+                if (T0 > 0) ok &= wait_flag_ge_warp_at(flags, f - t.nt1 * t.nts, t.sweep_units, tag, wc.spin);
+                if (T1 > 0) ok &= wait_flag_ge_warp_at(flags, f - t.nts, t.sweep_units, tag, wc.spin);
+                if (TS > 0) ok &= wait_flag_ge_warp_at(flags, f - 1, t.sweep_units, tag, wc.spin);
+                if (!ok && lane == 0) atomicExch(status, DEV_TIMEOUT);
                 __threadfence();
             }
         }
@@ -1568,7 +1588,8 @@ static int launch_sweepdag(const RunCtx& ctx, double* u, const WS& w, const Swee
     int nsm = 0, per_sm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int nthr = t.b0 * t.b1;
+    // whole warps (warp 0 claims and waits as one warp); threads past the tile's lines own no line
+    const int nthr = (t.b0 * t.b1 + 31) / 32 * 32;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nthr, 0);
     int64_t nblk = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
     if (nblk > t.sweep_units * T) nblk = t.sweep_units * T;
