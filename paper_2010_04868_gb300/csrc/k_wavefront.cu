@@ -1602,7 +1602,7 @@ static int launch_sweepdag(const RunCtx& ctx, double* u, const WS& w, const Swee
 // 2D Gauss-Seidel, rows as lanes (k_gs2d_rows): constant boundary, radius 1, constant weights, rows of
 // a multiple of four columns on a 32-byte-aligned grid (the dispatcher checks).
 // Sweeps go to launches of at most GR_MAX_TASKS tasks (progress words) each.
-constexpr int64_t GR_MAX_TASKS = (int64_t)1 << 20;
+constexpr int64_t GR_MAX_TASKS = (int64_t)1 << 18;  // 32 MiB of progress words at most
 
 template <int SHAPE, int CH>
 static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)

@@ -234,3 +234,13 @@ def test_gs2d_rows_stalled_task_times_out_without_hanging():
     ref = oracle_run(u0, 6, 2, "star", 1, w, "gs", "constant", 0.0, "fma")
     assert bits_equal(u.cpu().numpy(), ref)
     st.close()
+
+
+def test_gs2d_rows_many_sweeps_split_over_launches():
+    """More sweeps than one launch's progress words hold (2^18 tasks: 131072 sweeps of a 2-band grid):
+    the rows pipeline runs them in two launches and agrees with the one-warp tiles bit for bit."""
+    w, u0 = case(2, "star", 1, (64, 64), seed=21)
+    T = (1 << 17) + 5
+    a = gpu_run(u0, T, 2, "star", 1, w, "gs", "constant", 0.1, "fma", plan=WAVE, tile=ROWS)
+    b = gpu_run(u0, T, 2, "star", 1, w, "gs", "constant", 0.1, "fma", plan=WAVE, tile=(0, 0, 16))
+    assert bits_equal(a, b), first_diff(a, b)
