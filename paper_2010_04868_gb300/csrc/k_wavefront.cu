@@ -948,11 +948,15 @@ __device__ __forceinline__ Q4 shfl_up4(const Q4& q)
     return r;
 }
 
-template <int SHAPE, int ARITH, int CH>
-__global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u, RowGeo g, double c,
+// FIELD: per-point weights (the 5-point star only), fld holding the 5 planes of n0 x n1 weights in
+// canonical term order; each lane loads its own row's weights a step ahead of use.
+template <int SHAPE, int ARITH, int CH, bool FIELD = false>
+__global__ void __launch_bounds__(GR_THREADS, FIELD ? 2 : 3) k_gs2d_rows(double* __restrict__ u, RowGeo g, double c,
                                                           WArr<Stn<2, SHAPE, 1>::K> w, int* __restrict__ prog,
-                                                          int* __restrict__ ticket, int* status, WaitCfg wc)
+                                                          int* __restrict__ ticket, int* status, WaitCfg wc,
+                                                          const double* __restrict__ fld = nullptr)
 {
+    static_assert(!FIELD || SHAPE == STAR, "per-point weights: the 5-point star only");
     constexpr int SK = SHAPE == STAR ? 1 : 2;   // groups lane k trails lane k - 1
     constexpr int QX0 = SHAPE == STAR ? 0 : -1;  // first group of the x-row ring, relative to G
     constexpr int LX = QX0 + 4;                  // group the x-row ring loads at a step, relative to G
@@ -999,6 +1003,17 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
         Q4 RO[4], RX[4], O[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) O[q].v[0] = O[q].v[1] = O[q].v[2] = O[q].v[3] = c;
+        // FIELD: WR[m & 1][q] the weights of term q (summation order) at group G of step m
+        Q4 WR[FIELD ? 2 : 1][FIELD ? 5 : 1];
+        const int64_t fpl = g.n0 * g.n1;  // points per weight plane
+        auto ld_w = [&](int grp, Q4* dst) {
+            if constexpr (FIELD) {
+#pragma unroll
+                for (int q = 0; q < 5; ++q)
+                    dst[q] = ld_group(fld + (int64_t)(4 - q) * fpl + (row - u), grp, ng,
+                                      row_ok && (unsigned)grp < (unsigned)ng && GBST_IN(grp, ng), 0.0);
+            }
+        };
         for (int t0 = 0; t0 < steps; t0 += CH) {
             // every lane polls (one warp-wide load of one word, the same value to all lanes), so that
             // the warp never splits around the wait; timed_out stays uniform
@@ -1024,6 +1039,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
                 for (int q = 0; q < 4; ++q) RO[q] = ld_row(G0 + q);
 #pragma unroll
                 for (int q = QX0; q < QX0 + 4; ++q) RX[q & 3] = ld_x(G0 + q);
+                ld_w(G0, WR[0]);
             }
             for (int tg = t0; tg < t0 + CH; tg += 4) {
 #pragma unroll
@@ -1038,15 +1054,20 @@ __global__ void __launch_bounds__(GR_THREADS) k_gs2d_rows(double* __restrict__ u
                         if (lane == 31) bel = RX[m & 3];
                         if (lane == 0) abv = RX[m & 3];
                         double left = O[(m + 3) & 3].v[3];
+                        if constexpr (FIELD) ld_w(tg + m - SK * lane + 1, WR[(m + 1) & 1]);  // next step's
 #pragma unroll
                         for (int x = 0; x < 4; ++x) {
                             // (+1,0) (0,+1) (0,0) (0,-1) (-1,0)
+                            auto wt = [&](int q) -> double {
+                                if constexpr (FIELD) return WR[m & 1][q].v[x];
+                                return w.w[q];
+                            };
                             const double rgt = x < 3 ? RO[m & 3].v[x + 1] : RO[(m + 1) & 3].v[0];
-                            double acc = __dmul_rn(w.w[0], bel.v[x]);
-                            acc = acc_step<ARITH>(acc, w.w[1], rgt);
-                            acc = acc_step<ARITH>(acc, w.w[2], RO[m & 3].v[x]);
-                            acc = acc_step<ARITH>(acc, w.w[3], left);
-                            acc = acc_step<ARITH>(acc, w.w[4], abv.v[x]);
+                            double acc = __dmul_rn(wt(0), bel.v[x]);
+                            acc = acc_step<ARITH>(acc, wt(1), rgt);
+                            acc = acc_step<ARITH>(acc, wt(2), RO[m & 3].v[x]);
+                            acc = acc_step<ARITH>(acc, wt(3), left);
+                            acc = acc_step<ARITH>(acc, wt(4), abv.v[x]);
                             out.v[x] = acc;
                             left = acc;
                         }
@@ -1599,8 +1620,9 @@ static int launch_sweepdag(const RunCtx& ctx, double* u, const WS& w, const Swee
     return cuda_rc(cudaGetLastError());
 }
 
-// 2D Gauss-Seidel, rows as lanes (k_gs2d_rows): constant boundary, radius 1, constant weights, rows of
-// a multiple of four columns on a 32-byte-aligned grid (the dispatcher checks).
+// 2D Gauss-Seidel, rows as lanes (k_gs2d_rows): constant boundary, radius 1, constant weights (or a
+// weight field for the star), rows of a multiple of four columns on a 32-byte-aligned grid and field
+// (the dispatcher checks).
 // Sweeps go to launches of at most GR_MAX_TASKS tasks (progress words) each.
 constexpr int64_t GR_MAX_TASKS = (int64_t)1 << 18;  // 32 MiB of progress words at most
 
@@ -1625,7 +1647,13 @@ static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
     constexpr int K = Stn<2, SHAPE, 1>::K;
     WArr<K> w;
     for (int q = 0; q < K; ++q) w.w[q] = h->w_desc[q];
+    const bool field = ctx.sd.field != nullptr;
     auto kern = h->arith == ARITH_FMA ? k_gs2d_rows<SHAPE, ARITH_FMA, CH> : k_gs2d_rows<SHAPE, ARITH_UNFUSED, CH>;
+    if constexpr (SHAPE == STAR) {
+        if (field)
+            kern = h->arith == ARITH_FMA ? k_gs2d_rows<SHAPE, ARITH_FMA, CH, true>
+                                         : k_gs2d_rows<SHAPE, ARITH_UNFUSED, CH, true>;
+    }
     int nsm = 0, per_sm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1645,7 +1673,7 @@ static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
         if (cudaMemsetAsync(ticket, 0, 8, ctx.st) != cudaSuccess) return STENCIL_ECUDA;
         if (cudaMemsetAsync(prog, 0, (size_t)g.ntasks * GR_PSTRIDE * sizeof(int), ctx.st) != cudaSuccess)
             return STENCIL_ECUDA;
-        kern<<<(unsigned)nblk, GR_THREADS, 0, ctx.st>>>(u, g, h->c, w, prog, ticket, h->d_status, wc);
+        kern<<<(unsigned)nblk, GR_THREADS, 0, ctx.st>>>(u, g, h->c, w, prog, ticket, h->d_status, wc, ctx.sd.field);
         g_launches++;
         if (cudaGetLastError() != cudaSuccess) return STENCIL_ECUDA;
     }
@@ -1687,10 +1715,12 @@ static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, boo
         // (measured level with the one-warp tile at best, so not the default)
         const int64_t pw = ctx.wtile[2];
         const bool w8 = pw == 8;
-        // tile[2] = 0 (default) or 2: rows as lanes where they apply (radius 1, constant weights, rows of
-        // whole 32-byte groups of four columns); 16 or 8: the one-warp tiles with that many points per
-        // lane and step; 1: the decoupled tile. Other grids take the one-warp tiles.
-        const bool rows_ok = h->r == 1 && !ctx.sd.field && ctx.g.n2 % 4 == 0 && ((uintptr_t)u & 31) == 0;
+        // tile[2] = 0 (default) or 2: rows as lanes where they apply (radius 1, constant weights or
+        // the star's weight field, rows of whole 32-byte groups of four columns); 16 or 8: the one-warp
+        // tiles with that many points per lane and step; 1: the decoupled tile. Other grids take the
+        // one-warp tiles.
+        const bool rows_ok = h->r == 1 && ctx.g.n2 % 4 == 0 && ((uintptr_t)u & 31) == 0 &&
+                             (!ctx.sd.field || (h->shape == STAR && ((uintptr_t)ctx.sd.field & 31) == 0));
         if ((pw == 0 || pw == 2) && rows_ok)
             return h->shape == STAR ? gs2d_rows<STAR>(ctx, u, T, prep) : gs2d_rows<BOX>(ctx, u, T, prep);
         if (h->shape == STAR && h->r == 1)

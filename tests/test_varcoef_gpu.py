@@ -205,3 +205,24 @@ def test_jacobi2d_field_full_size():
     ref = _oracle(u0, 3, 2, "star", 1, field, "jacobi", "constant", 0.0, "fma")
     got = _gpu(u0, 3, 2, "star", 1, field, "jacobi", "constant", 0.0, "fma")
     assert bits_equal(got, ref), first_diff(got, ref)
+
+
+@pytest.mark.parametrize("ext", [(37, 132), (64, 64), (1, 8), (97, 36), (33, 68)])
+@pytest.mark.parametrize("c", [0.0, 0.2])
+def test_gs2d_rows_field_equals_oracle(ext, c):
+    """The 2D Gauss-Seidel wavefront's default plan with a weight field on whole groups of four
+    columns (rows as lanes, each lane loading its row's weights a step ahead): bit for bit."""
+    field, u0, _ = _case(2, "star", 1, ext, seed=700 + ext[0])
+    for T in (1, 5, 33):
+        for arith in ("fma", "unfused"):
+            ref = _oracle(u0, T, 2, "star", 1, field, "gs", "constant", c, arith)
+            got = _gpu(u0, T, 2, "star", 1, field, "gs", "constant", c, arith, plan=WAVE)
+            assert bits_equal(got, ref), (T, arith, first_diff(got, ref))
+
+
+def test_gs2d_rows_field_full_size():
+    """The 4096^2 field workload's grid (per-point weights), T cut to 12 for the serial oracle."""
+    field, u0, _ = _case(2, "star", 1, (4096, 4096), seed=415)
+    ref = _oracle(u0, 12, 2, "star", 1, field, "gs", "constant", 0.0, "fma")
+    got = _gpu(u0, 12, 2, "star", 1, field, "gs", "constant", 0.0, "fma", plan=WAVE)
+    assert bits_equal(got, ref), first_diff(got, ref)
