@@ -114,8 +114,9 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
  *            constant boundary, tile[0] = CTAs per SM of the persistent
  *            kernel, in 2D tile[1] = skewed rows per tile (2..64) and, in 2D
  *            with radius 1, tile[2] = 0 (default) or 2 for rows as lanes
- *            where they apply (one weight per term, rows of a multiple of 4
- *            columns, a 32-byte-aligned grid: a warp's lanes hold 32 rows of
+ *            where they apply (one weight per term or, for the 5-point
+ *            star, a weight field; rows of a multiple of 4 columns; a
+ *            32-byte-aligned grid and field: a warp's lanes hold 32 rows of
  *            one sweep, the sweeps pipelined across warps; tile[0] = CTAs of
  *            four warps per SM, tile[1] = steps between progress
  *            publications, 8 (default), 16, 64 or 128), 8 or 16 for the
