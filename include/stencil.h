@@ -112,10 +112,11 @@ int stencil_create(int dim, int shape, int radius, const double* coeffs, int nco
  *   tile     tile extents (slowest first) for BLOCKED; period lengths per axis
  *            (slowest first) for DIAMOND; for WAVEFRONT in 2D/3D with a
  *            constant boundary, tile[0] = CTAs per SM of the persistent
- *            kernel, in 2D tile[1] = skewed rows per tile (2..64) and, in 2D
- *            with radius 1, tile[2] = 0 (default) or 2 for rows as lanes
+ *            kernel, in 2D tile[1] = skewed rows per tile (2..64) and, in 2D,
+ *            tile[2] = 0 (default) or 2 for rows as lanes
  *            where they apply (one weight per term or, for the 5-point
- *            star, a weight field; rows of a multiple of 4 columns; a
+ *            star, a weight field; also the radius-2 star with one weight
+ *            per term; rows of a multiple of 4 columns; a
  *            32-byte-aligned grid and field: a warp's lanes hold 32 rows of
  *            one sweep, the sweeps pipelined across warps; tile[0] = CTAs of
  *            four warps per SM, tile[1] = steps between progress

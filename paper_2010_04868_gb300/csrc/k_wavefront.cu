@@ -932,33 +932,36 @@ __device__ __forceinline__ void st_group(double* p, const Q4& q)
                  : "memory");
 }
 
-__device__ __forceinline__ Q4 shfl_down4(const Q4& q)
+__device__ __forceinline__ Q4 shfl_down4(const Q4& q, int d = 1)
 {
     Q4 r;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) r.v[e] = __shfl_down_sync(FULL, q.v[e], 1);
+    for (int e = 0; e < 4; ++e) r.v[e] = __shfl_down_sync(FULL, q.v[e], d);
     return r;
 }
 
-__device__ __forceinline__ Q4 shfl_up4(const Q4& q)
+__device__ __forceinline__ Q4 shfl_up4(const Q4& q, int d = 1)
 {
     Q4 r;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) r.v[e] = __shfl_up_sync(FULL, q.v[e], 1);
+    for (int e = 0; e < 4; ++e) r.v[e] = __shfl_up_sync(FULL, q.v[e], d);
     return r;
 }
 
 // FIELD: per-point weights (the 5-point star only), fld holding the 5 planes of n0 x n1 weights in
 // canonical term order; each lane loads its own row's weights a step ahead of use.
-template <int SHAPE, int ARITH, int CH, bool FIELD = false>
-__global__ void __launch_bounds__(GR_THREADS, FIELD ? 2 : 3) k_gs2d_rows(double* __restrict__ u, RowGeo g, double c,
-                                                          WArr<Stn<2, SHAPE, 1>::K> w, int* __restrict__ prog,
+// R = 2: the 9-point star of radius 2; lanes 0 and 31 then hold a second row beyond the band (RY),
+// and lanes 1 and 30 take their outer neighbour row from lane 0's and lane 31's first ring.
+template <int SHAPE, int ARITH, int CH, bool FIELD = false, int R = 1>
+__global__ void __launch_bounds__(GR_THREADS, (FIELD || R == 2) ? 2 : 3) k_gs2d_rows(double* __restrict__ u, RowGeo g, double c,
+                                                          WArr<Stn<2, SHAPE, R>::K> w, int* __restrict__ prog,
                                                           int* __restrict__ ticket, int* status, WaitCfg wc,
                                                           const double* __restrict__ fld = nullptr)
 {
-    static_assert(!FIELD || SHAPE == STAR, "per-point weights: the 5-point star only");
+    static_assert(!FIELD || (SHAPE == STAR && R == 1), "per-point weights: the 5-point star only");
+    static_assert(R == 1 || (SHAPE == STAR && !FIELD), "radius 2: the star with one weight per term");
     constexpr int SK = SHAPE == STAR ? 1 : 2;   // groups lane k trails lane k - 1
-    constexpr int QX0 = SHAPE == STAR ? 0 : -1;  // first group of the x-row ring, relative to G
+    constexpr int QX0 = (SHAPE == STAR && R == 1) ? 0 : -1;  // first group of the x-row rings, relative to G
     constexpr int LX = QX0 + 4;                  // group the x-row ring loads at a step, relative to G
     const int lane = threadIdx.x & 31;
     const int64_t nprog = g.T * g.nb;  // progress words (bounds of the checked build)
@@ -985,6 +988,10 @@ __global__ void __launch_bounds__(GR_THREADS, FIELD ? 2 : 3) k_gs2d_rows(double*
         const int64_t ix = lane == 0 ? b * 32 - 1 : b * 32 + 32;
         const bool x_ok = (lane == 0 || lane == 31) && ix >= 0 && ix < g.n0;
         const double* xrow = x_ok ? u + ix * g.n1 : row;  // other lanes load (and drop) their own row
+        // R = 2: lane 0's second row above (32 b - 2), lane 31's second row below (32 b + 33)
+        const int64_t iy = lane == 0 ? b * 32 - 2 : b * 32 + 33;
+        const bool y_ok = R == 2 && (lane == 0 || lane == 31) && iy >= 0 && iy < g.n0;
+        const double* yrow = y_ok ? u + iy * g.n1 : row;
         const int64_t f = s * g.nb + b;
         const int64_t fA = f - 1, fO = f - g.nb, fB = f - g.nb + 1;  // above / own / below predecessors
         const bool hasA = b > 0, hasO = s > 0, hasB = s > 0 && b + 1 < g.nb;
@@ -996,11 +1003,14 @@ __global__ void __launch_bounds__(GR_THREADS, FIELD ? 2 : 3) k_gs2d_rows(double*
         auto ld_x = [&](int grp) -> Q4 {
             return ld_group(xrow, grp, ng, x_ok && (unsigned)grp < (unsigned)ng && GBST_IN(grp, ng), c);
         };
+        auto ld_y = [&](int grp) -> Q4 {
+            return ld_group(yrow, grp, ng, y_ok && (unsigned)grp < (unsigned)ng && GBST_IN(grp, ng), c);
+        };
         // RO[(m + q) & 3]: old values of this lane's row, group G + q (q = 0..3), G the group of step m;
         // RX[(m + q) & 3]: lane 0 the newest row above, lane 31 the old row below, group G + q
         //                  (q = QX0 .. QX0 + 3);
         // O[m & 3]: this lane's outputs of step m (c outside the grid)
-        Q4 RO[4], RX[4], O[4];
+        Q4 RO[4], RX[4], O[4], RY[R == 2 ? 4 : 1];
 #pragma unroll
         for (int q = 0; q < 4; ++q) O[q].v[0] = O[q].v[1] = O[q].v[2] = O[q].v[3] = c;
         // FIELD: WR[m & 1][q] the weights of term q (summation order) at group G of step m
@@ -1019,7 +1029,7 @@ __global__ void __launch_bounds__(GR_THREADS, FIELD ? 2 : 3) k_gs2d_rows(double*
             // the warp never splits around the wait; timed_out stays uniform
             if (!timed_out) {
                 bool ok = true;
-                const int nA = t0 + CH + LX + 31 * SK, nO = t0 + CH + 4, nB = t0 + CH - 31 * SK + LX;
+                const int nA = t0 + CH + LX + 31 * SK, nO = t0 + CH + 4, nB = t0 + CH - 31 * SK + LX + (R - 1);
                 if (hasA && GBST_IN(fA, nprog))
                     ok &= rows_wait(prog + fA * GR_PSTRIDE, nA < smax ? nA : smax, kA, wc.spin);
                 if (ok && hasO && GBST_IN(fO, nprog))
@@ -1039,6 +1049,10 @@ __global__ void __launch_bounds__(GR_THREADS, FIELD ? 2 : 3) k_gs2d_rows(double*
                 for (int q = 0; q < 4; ++q) RO[q] = ld_row(G0 + q);
 #pragma unroll
                 for (int q = QX0; q < QX0 + 4; ++q) RX[q & 3] = ld_x(G0 + q);
+                if constexpr (R == 2) {
+#pragma unroll
+                    for (int q = QX0; q < QX0 + 4; ++q) RY[q & 3] = ld_y(G0 + q);
+                }
                 ld_w(G0, WR[0]);
             }
             for (int tg = t0; tg < t0 + CH; tg += 4) {
@@ -1046,7 +1060,48 @@ __global__ void __launch_bounds__(GR_THREADS, FIELD ? 2 : 3) k_gs2d_rows(double*
                 for (int m = 0; m < 4; ++m) {
                     const int G = tg + m - SK * lane;
                     Q4 out;
-                    if (SHAPE == STAR) {
+                    if constexpr (R == 2) {
+                        // below: rows i + 1 (lane k + 1's q = 1) and i + 2 (lane k + 2's q = 2); above: lane
+                        // k - 1's output of step m - 1 and lane k - 2's of step m - 2 (both group G). Beyond
+                        // the band: lane 31 takes rows 32 b + 32 / 33 from its rings (q = 0), lane 30 the
+                        // first of them from lane 31's (its q = +1); lane 0 takes rows 32 b - 1 / - 2 from its
+                        // rings, lane 1 the first from lane 0's (its q = -1)
+                        Q4 b1 = shfl_down4(RO[(m + 1) & 3]);
+                        Q4 b2 = shfl_down4(RO[(m + 2) & 3], 2);
+                        const Q4 x31 = shfl_down4(RX[(m + 1) & 3]);
+                        Q4 a1 = shfl_up4(O[(m + 3) & 3]);
+                        Q4 a2 = shfl_up4(O[(m + 2) & 3], 2);
+                        const Q4 x0 = shfl_up4(RX[(m + 3) & 3]);
+                        if (lane == 30) b2 = x31;
+                        if (lane == 31) {
+                            b1 = RX[m & 3];
+                            b2 = RY[m & 3];
+                        }
+                        if (lane == 1) a2 = x0;
+                        if (lane == 0) {
+                            a1 = RX[m & 3];
+                            a2 = RY[m & 3];
+                        }
+                        double l1 = O[(m + 3) & 3].v[3], l2 = O[(m + 3) & 3].v[2];
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) {
+                            // (+2,0) (+1,0) (0,+2) (0,+1) (0,0) (0,-1) (0,-2) (-1,0) (-2,0)
+                            const double r1 = x < 3 ? RO[m & 3].v[x + 1] : RO[(m + 1) & 3].v[0];
+                            const double r2 = x < 2 ? RO[m & 3].v[x + 2] : RO[(m + 1) & 3].v[x - 2];
+                            double acc = __dmul_rn(w.w[0], b2.v[x]);
+                            acc = acc_step<ARITH>(acc, w.w[1], b1.v[x]);
+                            acc = acc_step<ARITH>(acc, w.w[2], r2);
+                            acc = acc_step<ARITH>(acc, w.w[3], r1);
+                            acc = acc_step<ARITH>(acc, w.w[4], RO[m & 3].v[x]);
+                            acc = acc_step<ARITH>(acc, w.w[5], l1);
+                            acc = acc_step<ARITH>(acc, w.w[6], l2);
+                            acc = acc_step<ARITH>(acc, w.w[7], a1.v[x]);
+                            acc = acc_step<ARITH>(acc, w.w[8], a2.v[x]);
+                            out.v[x] = acc;
+                            l2 = l1;
+                            l1 = acc;
+                        }
+                    } else if (SHAPE == STAR) {
                         // below: lane k + 1's own-row group G (its q = 1); above: lane k - 1's outputs of
                         // step m - 1 (its group then was G); lanes 31 and 0 take the x row's group G
                         Q4 bel = shfl_down4(RO[(m + 1) & 3]);
@@ -1126,6 +1181,7 @@ __global__ void __launch_bounds__(GR_THREADS, FIELD ? 2 : 3) k_gs2d_rows(double*
                     if (gin && row_ok && GBST_IN(G, ng)) st_group(row + 4 * (int64_t)G, out);
                     RO[m & 3] = ld_row(G + 4);
                     RX[(m + QX0) & 3] = ld_x(G + LX);
+                    if constexpr (R == 2) RY[(m + QX0) & 3] = ld_y(G + LX);
                 }
             }
             __syncwarp();
@@ -1626,7 +1682,7 @@ static int launch_sweepdag(const RunCtx& ctx, double* u, const WS& w, const Swee
 // Sweeps go to launches of at most GR_MAX_TASKS tasks (progress words) each.
 constexpr int64_t GR_MAX_TASKS = (int64_t)1 << 18;  // 32 MiB of progress words at most
 
-template <int SHAPE, int CH>
+template <int SHAPE, int CH, int R>
 static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
 {
     stencil_handle_s* h = ctx.h;
@@ -1644,12 +1700,13 @@ static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
     if (rc || prepare_only) return rc;
     int* ticket = (int*)h->wave_ws;
     int* prog = (int*)((char*)h->wave_ws + 256);
-    constexpr int K = Stn<2, SHAPE, 1>::K;
+    constexpr int K = Stn<2, SHAPE, R>::K;
     WArr<K> w;
     for (int q = 0; q < K; ++q) w.w[q] = h->w_desc[q];
     const bool field = ctx.sd.field != nullptr;
-    auto kern = h->arith == ARITH_FMA ? k_gs2d_rows<SHAPE, ARITH_FMA, CH> : k_gs2d_rows<SHAPE, ARITH_UNFUSED, CH>;
-    if constexpr (SHAPE == STAR) {
+    auto kern = h->arith == ARITH_FMA ? k_gs2d_rows<SHAPE, ARITH_FMA, CH, false, R>
+                                      : k_gs2d_rows<SHAPE, ARITH_UNFUSED, CH, false, R>;
+    if constexpr (SHAPE == STAR && R == 1) {
         if (field)
             kern = h->arith == ARITH_FMA ? k_gs2d_rows<SHAPE, ARITH_FMA, CH, true>
                                          : k_gs2d_rows<SHAPE, ARITH_UNFUSED, CH, true>;
@@ -1681,13 +1738,13 @@ static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
 }
 
 // steps per chunk of the rows pipeline: 8, or 16 / 64 / 128 when the wavefront plan asks (tile[1])
-template <int SHAPE>
+template <int SHAPE, int R>
 static int gs2d_rows(const RunCtx& ctx, double* u, int64_t T, bool prepare_only)
 {
-    if (ctx.wtile[1] == 16) return gs2d_rows<SHAPE, 16>(ctx, u, T, prepare_only);
-    if (ctx.wtile[1] == 64) return gs2d_rows<SHAPE, 64>(ctx, u, T, prepare_only);
-    if (ctx.wtile[1] == 128) return gs2d_rows<SHAPE, 128>(ctx, u, T, prepare_only);
-    return gs2d_rows<SHAPE, GR_CHUNK>(ctx, u, T, prepare_only);  // 8 steps
+    if (ctx.wtile[1] == 16) return gs2d_rows<SHAPE, 16, R>(ctx, u, T, prepare_only);
+    if (ctx.wtile[1] == 64) return gs2d_rows<SHAPE, 64, R>(ctx, u, T, prepare_only);
+    if (ctx.wtile[1] == 128) return gs2d_rows<SHAPE, 128, R>(ctx, u, T, prepare_only);
+    return gs2d_rows<SHAPE, GR_CHUNK, R>(ctx, u, T, prepare_only);  // 8 steps
 }
 
 static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, bool prep)
@@ -1715,14 +1772,19 @@ static int wave_dispatch(const RunCtx& ctx, double* u, int64_t T, int lanes, boo
         // (measured level with the one-warp tile at best, so not the default)
         const int64_t pw = ctx.wtile[2];
         const bool w8 = pw == 8;
-        // tile[2] = 0 (default) or 2: rows as lanes where they apply (radius 1, constant weights or
-        // the star's weight field, rows of whole 32-byte groups of four columns); 16 or 8: the one-warp
+        // tile[2] = 0 (default) or 2: rows as lanes where they apply (radius 1 with constant weights or
+        // the star's weight field, the radius-2 star with constant weights; rows of whole 32-byte
+        // groups of four columns); 16 or 8: the one-warp
         // tiles with that many points per lane and step; 1: the decoupled tile. Other grids take the
         // one-warp tiles.
-        const bool rows_ok = h->r == 1 && ctx.g.n2 % 4 == 0 && ((uintptr_t)u & 31) == 0 &&
-                             (!ctx.sd.field || (h->shape == STAR && ((uintptr_t)ctx.sd.field & 31) == 0));
-        if ((pw == 0 || pw == 2) && rows_ok)
-            return h->shape == STAR ? gs2d_rows<STAR>(ctx, u, T, prep) : gs2d_rows<BOX>(ctx, u, T, prep);
+        const bool rows_ok =
+            ctx.g.n2 % 4 == 0 && ((uintptr_t)u & 31) == 0 &&
+            ((h->r == 1 && (!ctx.sd.field || (h->shape == STAR && ((uintptr_t)ctx.sd.field & 31) == 0))) ||
+             (h->r == 2 && h->shape == STAR && !ctx.sd.field));
+        if ((pw == 0 || pw == 2) && rows_ok) {
+            if (h->r == 2) return gs2d_rows<STAR, 2>(ctx, u, T, prep);
+            return h->shape == STAR ? gs2d_rows<STAR, 1>(ctx, u, T, prep) : gs2d_rows<BOX, 1>(ctx, u, T, prep);
+        }
         if (h->shape == STAR && h->r == 1)
             return w8 ? wave_tiles<2, STAR, 1, 8>(ctx, u, T, lanes, prep)
                       : wave_tiles<2, STAR, 1, 16>(ctx, u, T, lanes, prep, pw == 1 && !ctx.sd.field);

@@ -244,3 +244,26 @@ def test_gs2d_rows_many_sweeps_split_over_launches():
     a = gpu_run(u0, T, 2, "star", 1, w, "gs", "constant", 0.1, "fma", plan=WAVE, tile=ROWS)
     b = gpu_run(u0, T, 2, "star", 1, w, "gs", "constant", 0.1, "fma", plan=WAVE, tile=(0, 0, 16))
     assert bits_equal(a, b), first_diff(a, b)
+
+
+@pytest.mark.parametrize("ext", [(1, 4), (2, 8), (3, 12), (31, 64), (33, 68), (64, 36), (97, 132), (130, 76)])
+@pytest.mark.parametrize("c", [0.0, 0.3])
+def test_gs2d_rows_radius2_star_equals_oracle(ext, c):
+    """Rows as lanes for the 9-point star of radius 2 (lanes 0/1 and 30/31 reach two rows beyond the
+    band): ragged bands, both rounding modes, bit for bit."""
+    w, u0 = case(2, "star", 2, ext, seed=ext[0] + 5 * ext[1])
+    for T in (1, 2, 5, 33):
+        for arith in ("fma", "unfused"):
+            ref = oracle_run(u0, T, 2, "star", 2, w, "gs", "constant", c, arith)
+            got = gpu_run(u0, T, 2, "star", 2, w, "gs", "constant", c, arith, plan=WAVE, tile=ROWS)
+            assert bits_equal(got, ref), (T, arith, first_diff(got, ref))
+
+
+def test_gs2d_rows_radius2_full_size_equals_oracle():
+    """The 4096^2 radius-2 Gauss-Seidel workload's grid with rows as lanes (its default plan), T cut to 12."""
+    from paper_2010_04868_gb300 import inputs
+    u0 = inputs.grid(inputs.SEED_BASE + 3, (4096, 4096))
+    w = inputs.normalized_weights(inputs.SEED_BASE + 319, 9)
+    ref = oracle_run(u0, 12, 2, "star", 2, w, "gs", "constant", 0.0, "fma")
+    got = gpu_run(u0, 12, 2, "star", 2, w, "gs", "constant", 0.0, "fma", plan=WAVE)
+    assert bits_equal(got, ref), first_diff(got, ref)
