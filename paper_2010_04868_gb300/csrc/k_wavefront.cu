@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
 // previous-sweep terms of a point (lane k - 1's outputs at x and x + 1, made
 // at steps j - 33 and j - 32) are known two batches of 16 steps before the
 // point is due, so they can be summed away from the chain:
-//   warps 1-3 and 5-7 (producers) form P = w(+1) u'(x+1) (+) w(0) u'(x) for the next
+//   warps 1-6 (producers) form P = w(+1) u'(x+1) (+) w(0) u'(x) for the next
 //             batch of 16 steps, each warp a share of the steps, all 32 lanes
 //             (unrolled, so that their sums overlap);
 //   warp 0 (the chain) does the 16 dependent updates u(x) = P (+) w(-1) u(x-1)
@@ -226,14 +226,13 @@ __global__ void __launch_bounds__(32) k_gs1d_wave(double* __restrict__ u, int64_
 // one CTA barrier per batch instead of one per step. The chain's outputs go to
 // a shared ring of 3 batches (the producers read the two before the current
 // one); lane 0's previous-sweep values are the previous block's outputs, which
-// warp 4 (I/O) fetches from the grid two batches ahead with cp.async (a CTA barrier
+// warp 7 fetches from the grid two batches ahead with cp.async (a CTA barrier
 // waits for a warp's outstanding register loads, not for cp.async), behind the
 // same progress words as above, stores the last lane's outputs (the block's
 // final sweep) and publishes this block's progress every 4 batches, with the
 // fence at the start of the next batch where it overlaps the chain. The sum keeps the
 // descending order and rounding of every other kernel.
 constexpr int W4_S = 33, W4_D = 16, W4_ROWS = 3 * W4_D;
-constexpr int W4_IO = 4;  // the I/O warp (on the chain warp's SM sub-partition)
 
 // Partial sums of steps D0 .. D1 - 1 of batch m for every lane (k = lane), unrolled so that the
 // independent sums of the steps overlap. rbm = (16 m) mod 48, the ring row of the batch's first step.
@@ -275,10 +274,6 @@ __global__ void __launch_bounds__(256) k_gs1d_wave4(double* __restrict__ u, int6
                                                     unsigned tag, WaitCfg wc)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // roles: warp 0 the chain, warp W4_IO the grid and progress I/O, the other six the partial sums
-    // (producer pi = 1..6); warps w and w + 4 share an SM sub-partition, so the chain's FP64 unit is
-    // shared only with the I/O warp, which issues no FP64 work
-    const int pi = (warp == 0 || warp == W4_IO) ? 0 : (warp < W4_IO ? warp : warp - 1);
     __shared__ int s_b;
     __shared__ double O[W4_ROWS][32];      // outputs: row = step mod 48, column = lane
     __shared__ double Pb[2][W4_D][32];     // producers' partial sums: batch parity, step in batch, lane
@@ -294,15 +289,15 @@ __global__ void __launch_bounds__(256) k_gs1d_wave4(double* __restrict__ u, int6
     const bool publish = b != wc.stall;
     const unsigned long long mytag = (unsigned long long)tag << PROG_SHIFT;
     const int64_t jmax = n - 1 + (int64_t)W4_S * (L - 1), mmax = jmax / W4_D;
-    int64_t known = b > 0 ? 0 : INT64_MAX;  // I/O warp: positions the previous block has finalised
+    int64_t known = b > 0 ? 0 : INT64_MAX;  // warp 7: positions the previous block has finalised
 
-    // I/O warp: positions [16m, 16m + 32) of the previous block's output into BOT by cp.async (the
+    // warp 7: positions [16m, 16m + 32) of the previous block's output into BOT by cp.async (the
     // CTA barrier does not wait for it, a register load would hold the barrier for an L2 round trip)
     auto bot_fetch = [&](int64_t m) {
         const int64_t lo = W4_D * m;
         if (lo >= n) return;
         const int64_t need = lo + 32 < n ? lo + 32 : n;
-        if (need > known) known = wait_progress_warp(prev, need, tag, status, wc.spin);  // the warp as one
+        if (need > known) known = wait_progress_warp(prev, need, tag, status, wc.spin);  // warp 7 as one
         const int64_t x = lo + lane;
         double* dst = BOT + (x & 63);
         if (x < n) {
@@ -317,7 +312,7 @@ __global__ void __launch_bounds__(256) k_gs1d_wave4(double* __restrict__ u, int6
     auto bot_landed = [&]() { asm volatile("cp.async.wait_all;" ::: "memory"); };
     auto produce = [&](int64_t m) {
         const int rbm = (int)((W4_D * m) % W4_ROWS);
-        switch (pi) {
+        switch (warp) {
             case 1: w4_produce<ARITH, 0, 3>(m, mmax, rbm, L, n, c, w, O, Pb, BOT); break;
             case 2: w4_produce<ARITH, 3, 6>(m, mmax, rbm, L, n, c, w, O, Pb, BOT); break;
             case 3: w4_produce<ARITH, 6, 9>(m, mmax, rbm, L, n, c, w, O, Pb, BOT); break;
@@ -329,7 +324,7 @@ __global__ void __launch_bounds__(256) k_gs1d_wave4(double* __restrict__ u, int6
     };
 
     // prologue: the previous block's first 64 positions, the partial sums of batch 0
-    if (warp == W4_IO) {
+    if (warp == 7) {
         bot_fetch(0);
         bot_fetch(1);
         bot_landed();
@@ -340,7 +335,7 @@ __global__ void __launch_bounds__(256) k_gs1d_wave4(double* __restrict__ u, int6
     __syncthreads();
 
     double nw = c;         // chain: this lane's previous output (the left neighbour of its next point)
-    int64_t pending = -1;  // I/O warp: progress to publish at the start of the next batch
+    int64_t pending = -1;  // warp 7: progress to publish at the start of the next batch
     for (int64_t m = 0; m <= mmax + 1; ++m) {
         if (warp == 0) {
             if (m <= mmax) {
@@ -374,7 +369,7 @@ __global__ void __launch_bounds__(256) k_gs1d_wave4(double* __restrict__ u, int6
                     }
                 }
             }
-        } else if (warp != W4_IO) {
+        } else if (warp < 7) {
             produce(m + 1);
         } else {
             // progress for the final-sweep stores of earlier batches, first: the fence overlaps the chain
@@ -403,8 +398,8 @@ __global__ void __launch_bounds__(256) k_gs1d_wave4(double* __restrict__ u, int6
         }
         __syncthreads();
     }
-    if (warp == W4_IO) bot_landed();                // no copy into shared memory outlives the CTA
-    if (threadIdx.x == 32 * W4_IO && publish) {     // the I/O warp, after its last stores
+    if (warp == 7) bot_landed();         // no copy into shared memory outlives the CTA
+    if (threadIdx.x == 224 && publish) {  // warp 7, after its last stores
         __threadfence();
         st_release64(mine, mytag | (unsigned long long)n);
     }
