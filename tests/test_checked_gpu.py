@@ -162,3 +162,29 @@ def test_checked_coefficient_field(dim, method, plan, ext):
     got = u.cpu().numpy()
     st.close()
     assert bits_equal(got, ref), first_diff(got, ref)
+
+
+@pytest.mark.parametrize("shape,r,ext", [("star", 1, (70, 44)), ("box", 1, (33, 68)), ("star", 2, (97, 36)),
+                                         ("star", 1, (1, 8))])
+def test_checked_wavefront_rows(shape, r, ext):
+    """The 2D wavefront's default plan on whole groups of four columns: rows as lanes."""
+    w, u0 = case(2, shape, r, ext, seed=ext[0] + r)
+    _check(u0, 9, 2, shape, r, w, "gs", "constant", 0.3, WAVE)
+
+
+def test_checked_wavefront_rows_field():
+    import torch
+    import oracle
+    from paper_2010_04868_gb300 import inputs, stencil as S
+    ext = (45, 64)
+    field = inputs.normalized_field(91, 5, ext)
+    u0 = inputs.grid(92, ext)
+    ref = oracle.run(u0, 6, dim=2, shape=0, r=1, weights=[0.0] * 5, method=1, bc=0, c=0.1, arith=0, field=field)
+    st = S.Stencil(2, 0, 1, [1.0] * 5, 1, 0, 0.1, 0).set_plan(WAVE)
+    st.set_field(torch.from_numpy(np.ascontiguousarray(field)).cuda())
+    u = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
+    st.run(u, 6)
+    assert st.status() == S.STENCIL_OK
+    got = u.cpu().numpy()
+    st.close()
+    assert bits_equal(got, ref), first_diff(got, ref)
