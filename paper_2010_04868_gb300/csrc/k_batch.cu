@@ -392,29 +392,21 @@ __global__ void __launch_bounds__(BT, 2) k_batch(const BProb* __restrict__ probs
     __shared__ int s_off[3 * BMAXK];
     __shared__ long long s_lo[BMAXK];
     for (;;) {
-        if (threadIdx.x < 32) {
-            // claim: the first problem (longest dependence chain first) whose next unit's phase is open.
-            // Warp 0 claims and waits as one warp (lane 0's loads and ticket broadcast), so that it never
-            // splits around the waits: a warp whose lane 0 alone polled while the others waited was
-            // measured to run its following work several times slower, and every warp of the CTA waits
-            // for it at the unit's barriers.
-            constexpr unsigned ALL = 0xffffffffu;
-            const int lane = threadIdx.x;
+        if (threadIdx.x == 0) {
+            // claim: the first problem (longest dependence chain first) whose next unit's phase is open
             int p = -1;
             long long tk = 0;
             for (int spin = 0; spin < BSPIN && p < 0; ++spin) {
                 bool all_out = true;
                 for (int oi = 0; oi < np && p < 0; ++oi) {
                     const BProb& Q = probs[order[oi]];
-                    const unsigned long long nx = __shfl_sync(ALL, ld_relaxed64(Q.next), 0);
+                    const unsigned long long nx = ld_relaxed64(Q.next);
                     if (nx >= (unsigned long long)Q.total) continue;
                     all_out = false;
                     int64_t uu;
                     const int64_t ph = phase_of(Q, (int64_t)nx, uu);
-                    if (__shfl_sync(ALL, ld_relaxed64(Q.done), 0) < (unsigned long long)units_before(Q, ph)) continue;
-                    unsigned long long t = 0;
-                    if (lane == 0) t = atomicAdd(Q.next, 1ull);
-                    t = __shfl_sync(ALL, t, 0);
+                    if (ld_relaxed64(Q.done) < (unsigned long long)units_before(Q, ph)) continue;
+                    const unsigned long long t = atomicAdd(Q.next, 1ull);
                     if (t >= (unsigned long long)Q.total) continue;
                     p = order[oi];
                     tk = (long long)t;
@@ -422,23 +414,21 @@ __global__ void __launch_bounds__(BT, 2) k_batch(const BProb* __restrict__ probs
                 if (all_out) break;
                 if (p < 0) __nanosleep(spin < 64 ? 32 : 128);
             }
-            if (lane == 0) s_p = p;
+            s_p = p;
             if (p >= 0) {
                 const BProb& Q = probs[p];
                 int64_t uu;
                 const int64_t ph = phase_of(Q, tk, uu);
-                if (lane == 0) {
-                    s_ph = ph;
-                    s_unit = uu;
-                }
+                s_ph = ph;
+                s_unit = uu;
                 // a unit claimed ahead of its phase waits for the units claimed before it
                 const unsigned long long need = (unsigned long long)units_before(Q, ph);
                 int it = 0;
-                while (__shfl_sync(ALL, ld_acq64(Q.done), 0) < need && it < BSPIN) {
+                while (ld_acq64(Q.done) < need && it < BSPIN) {
                     __nanosleep(it < 64 ? 32 : 128);
                     ++it;
                 }
-                if (it >= BSPIN && lane == 0) atomicExch(Q.status, DEV_TIMEOUT);
+                if (it >= BSPIN) atomicExch(Q.status, DEV_TIMEOUT);
                 __threadfence();
             }
         }
