@@ -150,19 +150,20 @@ __global__ void __launch_bounds__(256) k_jacobi_blocked(const __grid_constant__ 
             return;
         }
     } else {
-        for (int64_t idx = threadIdx.x; idx < region; idx += nthr) {
-            const int s2 = (int)(idx % b.E2);
-            const int s1 = (int)((idx / b.E2) % b.E1);
-            const int s0 = (int)(idx / ((int64_t)b.E2 * b.E1));
+        // the staged region fits in shared memory: 32-bit cell indices (E0 = 1 in 2D, E0 = E1 = 1 in 1D)
+        for (int idx = threadIdx.x; idx < (int)region; idx += nthr) {
+            const int s2 = DIM == 1 ? idx : idx % b.E2;
+            const int s1 = DIM == 1 ? 0 : DIM == 2 ? idx / b.E2 : (idx / b.E2) % b.E1;
+            const int s0 = DIM <= 2 ? 0 : idx / (b.E2 * b.E1);
             st_in(bufA, idx, region, fetch_bc(in, g0 + s0, g1 + s1, g2 + s2, g, bc, c));
         }
     }
     // cells outside the grid hold the boundary value in both buffers
     if (bc == BC_CONSTANT) {
-        for (int64_t idx = threadIdx.x; idx < region; idx += nthr) {
-            const int64_t i = g0 + idx / ((int64_t)b.E2 * b.E1);
-            const int64_t j = g1 + (idx / b.E2) % b.E1;
-            const int64_t k = g2 + idx % b.E2;
+        for (int idx = threadIdx.x; idx < (int)region; idx += nthr) {
+            const int64_t i = g0 + (DIM <= 2 ? 0 : idx / (b.E2 * b.E1));
+            const int64_t j = g1 + (DIM == 1 ? 0 : DIM == 2 ? idx / b.E2 : (idx / b.E2) % b.E1);
+            const int64_t k = g2 + (DIM == 1 ? idx : idx % b.E2);
             if (i < 0 || i >= g.n0 || j < 0 || j >= g.n1 || k < 0 || k >= g.n2) {
                 st_in(bufA, idx, region, c);
                 st_in(bufB, idx, region, c);
@@ -180,18 +181,40 @@ __global__ void __launch_bounds__(256) k_jacobi_blocked(const __grid_constant__ 
         const int lo0 = DIM >= 3 ? s * R : 0, hi0 = DIM >= 3 ? b.E0 - s * R : 1;
         const int lo1 = DIM >= 2 ? s * R : 0, hi1 = DIM >= 2 ? b.E1 - s * R : 1;
         const int lo2 = pad2 + s * R, hi2 = pad2 + b.B2 + 2 * b.h2 - s * R;
-        const int w1 = hi1 - lo1, w2 = hi2 - lo2;
-        const int64_t cnt = (int64_t)(hi0 - lo0) * w1 * w2;
-        for (int64_t idx = threadIdx.x; idx < cnt; idx += nthr) {
-            const int s2 = lo2 + (int)(idx % w2);
-            const int s1 = lo1 + (int)((idx / w2) % w1);
-            const int s0 = lo0 + (int)(idx / ((int64_t)w2 * w1));
+        const int w1 = hi1 - lo1, w2 = hi2 - lo2;  // >= 1: the halo is T_b * R wide on every used axis
+        auto cell = [&](int s0, int s1, int s2) {
             if (bc == BC_CONSTANT) {
                 const int64_t i = g0 + s0, j = g1 + s1, k = g2 + s2;
-                if (i < 0 || i >= g.n0 || j < 0 || j >= g.n1 || k < 0 || k >= g.n2) continue;
+                if (i < 0 || i >= g.n0 || j < 0 || j >= g.n1 || k < 0 || k >= g.n2) return;
             }
             const int64_t p = s0 * st0 + s1 * st1 + s2;
             st_in(dst, p, region, update_interior<DIM, SHAPE, R, ARITH, false>(src, p, st0, st1, w, region));
+        };
+        if (DIM == 1) {
+            for (int s2 = lo2 + (int)threadIdx.x; s2 < hi2; s2 += nthr) cell(0, 0, s2);
+        } else {
+            // Each thread walks its cells (s0, s1, s2) in steps of nthr cells without a division: the
+            // step is split once into (dq0, dq1, dr) and added digit by digit with carries. Both
+            // remainders are below their extents, so one subtraction per digit restores the range.
+            const int cnt = (hi0 - lo0) * w1 * w2;
+            const int dr = nthr % w2, dq = nthr / w2, dq1 = dq % w1, dq0 = dq / w1;
+            int s2 = lo2 + (int)threadIdx.x % w2;
+            int s1 = lo1 + ((int)threadIdx.x / w2) % w1;
+            int s0 = lo0 + (int)threadIdx.x / (w2 * w1);
+            for (int idx = threadIdx.x; idx < cnt; idx += nthr) {
+                cell(s0, s1, s2);
+                s2 += dr;
+                s1 += dq1;
+                s0 += dq0;
+                if (s2 >= hi2) {
+                    s2 -= w2;
+                    ++s1;
+                }
+                if (s1 >= hi1) {
+                    s1 -= w1;
+                    ++s0;
+                }
+            }
         }
         __syncthreads();
         double* tmp = src;
@@ -200,11 +223,11 @@ __global__ void __launch_bounds__(256) k_jacobi_blocked(const __grid_constant__ 
     }
 
     // ---- write the interior back
-    const int64_t cnt = (int64_t)b.B0 * b.B1 * b.B2;
-    for (int64_t idx = threadIdx.x; idx < cnt; idx += nthr) {
-        const int l2 = (int)(idx % b.B2);
-        const int l1 = (int)((idx / b.B2) % b.B1);
-        const int l0 = (int)(idx / ((int64_t)b.B2 * b.B1));
+    const int cnt = b.B0 * b.B1 * b.B2;
+    for (int idx = threadIdx.x; idx < cnt; idx += nthr) {
+        const int l2 = DIM == 1 ? idx : idx % b.B2;
+        const int l1 = DIM == 1 ? 0 : DIM == 2 ? idx / b.B2 : (idx / b.B2) % b.B1;
+        const int l0 = DIM <= 2 ? 0 : idx / (b.B2 * b.B1);
         const int64_t i = T0 * b.B0 + l0, j = T1 * b.B1 + l1, k = T2 * b.B2 + l2;
         if (i < g.n0 && j < g.n1 && k < g.n2)
             st_in(out, (i * g.n1 + j) * g.n2 + k, g.n0 * g.n1 * g.n2,
