@@ -256,8 +256,9 @@ __device__ __noinline__ void unit_jblock(const BProb& P, int64_t ph, int64_t uni
     if (!GBST_IN(((region + 31) & ~int64_t(31)) + region - 1, (int64_t)(dyn_smem_bytes() / 8))) return;
     const int64_t st1 = P.E2, st0 = (int64_t)P.E1 * P.E2;
     for (int q = threadIdx.x; q < P.K; q += BT) lo[q] = (long long)so[3 * q] * st0 + so[3 * q + 1] * st1 + so[3 * q + 2];
-    for (int64_t idx = threadIdx.x; idx < region; idx += BT) {
-        const int64_t i = g0 + idx / st0, j = g1 + (idx / st1) % P.E1, k = g2 + idx % st1;
+    // the staged region fits in shared memory: 32-bit cell indices
+    for (int idx = threadIdx.x; idx < (int)region; idx += BT) {
+        const int64_t i = g0 + idx / (P.E1 * P.E2), j = g1 + (idx / P.E2) % P.E1, k = g2 + idx % P.E2;
         A[idx] = fetch_bc(src, i, j, k, P.g, P.bc, P.c);
         if (P.bc == BC_CONSTANT && (i < 0 || i >= P.g.n0 || j < 0 || j >= P.g.n1 || k < 0 || k >= P.g.n2)) B[idx] = P.c;
     }
@@ -268,25 +269,47 @@ __device__ __noinline__ void unit_jblock(const BProb& P, int64_t ph, int64_t uni
         const int lo0 = P.dim >= 3 ? st * P.r : 0, hi0 = P.dim >= 3 ? P.E0 - st * P.r : 1;
         const int lo1 = P.dim >= 2 ? st * P.r : 0, hi1 = P.dim >= 2 ? P.E1 - st * P.r : 1;
         const int lo2 = st * P.r, hi2 = P.E2 - st * P.r;
-        const int w1 = hi1 - lo1, w2 = hi2 - lo2;
-        const int64_t cnt = (int64_t)(hi0 - lo0) * w1 * w2;
-        for (int64_t idx = threadIdx.x; idx < cnt; idx += BT) {
-            const int s2 = lo2 + (int)(idx % w2), s1 = lo1 + (int)((idx / w2) % w1), s0 = lo0 + (int)(idx / ((int64_t)w2 * w1));
+        const int w1 = hi1 - lo1, w2 = hi2 - lo2;  // >= 1: the halo is tb * r wide on every used axis
+        auto cell = [&](int s0, int s1, int s2) {
             if (P.bc == BC_CONSTANT) {
                 const int64_t i = g0 + s0, j = g1 + s1, k = g2 + s2;
-                if (i < 0 || i >= P.g.n0 || j < 0 || j >= P.g.n1 || k < 0 || k >= P.g.n2) continue;
+                if (i < 0 || i >= P.g.n0 || j < 0 || j >= P.g.n1 || k < 0 || k >= P.g.n2) return;
             }
             const int64_t p = s0 * st0 + s1 * st1 + s2;
             st_in(d, p, region, point_lin<ARITH>(s, p, lo, sw, P.K, region));
+        };
+        if (P.dim == 1) {
+            for (int s2 = lo2 + (int)threadIdx.x; s2 < hi2; s2 += BT) cell(0, 0, s2);
+        } else {
+            // each thread advances its (s0, s1, s2) by the digits of BT with carries: no division per cell
+            const int cnt = (hi0 - lo0) * w1 * w2;
+            const int dr = BT % w2, dq = BT / w2, dq1 = dq % w1, dq0 = dq / w1;
+            int s2 = lo2 + (int)threadIdx.x % w2;
+            int s1 = lo1 + ((int)threadIdx.x / w2) % w1;
+            int s0 = lo0 + (int)threadIdx.x / (w2 * w1);
+            for (int idx = threadIdx.x; idx < cnt; idx += BT) {
+                cell(s0, s1, s2);
+                s2 += dr;
+                s1 += dq1;
+                s0 += dq0;
+                if (s2 >= hi2) {
+                    s2 -= w2;
+                    ++s1;
+                }
+                if (s1 >= hi1) {
+                    s1 -= w1;
+                    ++s0;
+                }
+            }
         }
         __syncthreads();
         double* t = s;
         s = d;
         d = t;
     }
-    const int64_t cnt = (int64_t)P.B0 * P.B1 * P.B2;
-    for (int64_t idx = threadIdx.x; idx < cnt; idx += BT) {
-        const int l2 = (int)(idx % P.B2), l1 = (int)((idx / P.B2) % P.B1), l0 = (int)(idx / ((int64_t)P.B2 * P.B1));
+    const int cnt = P.B0 * P.B1 * P.B2;
+    for (int idx = threadIdx.x; idx < cnt; idx += BT) {
+        const int l2 = idx % P.B2, l1 = (idx / P.B2) % P.B1, l0 = idx / (P.B2 * P.B1);
         const int64_t i = T0 * P.B0 + l0, j = T1 * P.B1 + l1, k = T2 * P.B2 + l2;
         if (i < P.g.n0 && j < P.g.n1 && k < P.g.n2)
             st_in(dst, (i * P.g.n1 + j) * P.g.n2 + k, P.g.n0 * P.g.n1 * P.g.n2,
